@@ -1,0 +1,287 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- the definition (brute force over every input), closed forms derived
+from the constraint kinds of Sec. V-B, the paper's worked examples (Figs.
+1-5, Sec. VI-A), model re-verification, and an independent RUP checker."""
+import glob
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from closed_forms import (bounds_algebra, bounds_enum, partition_algebra,
+                          partition_enum)
+from ir_eval import cnf_satisfied, evaluate
+from workloads import queries
+from workloads.ir import IR, parse_text
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def solve_ir(ir_arr, trace=False):
+    cnf = oracle.encode(ir_arr)
+    res = oracle.dpll(cnf, want_trace=trace)
+    return cnf, res
+
+
+def model_words(cnf, model):
+    words, off = [], 0
+    for w in cnf.free_width:
+        v = 0
+        for k in range(int(w)):
+            v |= int(model[int(cnf.in_map[off + k]) - 1]) << k
+        words.append(v)
+        off += int(w)
+    return words
+
+
+# ---------------------------------------------------------------------------
+# Worked examples from the paper (tests/golden/*.sq)
+# ---------------------------------------------------------------------------
+
+def _golden_files():
+    return sorted(glob.glob(os.path.join(GOLDEN, "*.sq")))
+
+
+@pytest.mark.parametrize("path", _golden_files(), ids=lambda p: os.path.basename(p))
+def test_worked_examples(path):
+    ir, meta = parse_text(open(path).read())
+    assert "cite" in meta and meta["expect"] in ("SAT", "UNSAT")
+    a = ir.to_array()
+    cnf, res = solve_ir(a)
+    want = oracle.SAT if meta["expect"] == "SAT" else oracle.UNSAT
+    assert res["verdict"] == want
+    if want == oracle.SAT:
+        assert evaluate(a, model_words(cnf, res["model"]))
+    elif res["decisions"] <= 5000:
+        res = oracle.dpll(cnf, want_trace=True)
+        assert oracle.rup_check(cnf, res["trace"]) == 1
+    bits = sum(ir.free_widths())
+    if bits <= 26:
+        bf, wit = oracle.brute_force(a, max_bits=26)
+        assert bf == want
+    # at least one independent pin besides the stored expectation
+    assert want == oracle.SAT or res["decisions"] <= 5000 or bits <= 26
+
+
+# ---------------------------------------------------------------------------
+# Brute force over every input (the definition) on the query families
+# ---------------------------------------------------------------------------
+
+def _bounds_params(w, count, seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(count):
+        yield dict(w=w, k1=int(rng.integers(1, 5)), k0=int(rng.integers(0, 8)),
+                   a=int(rng.integers(1, 5)), c=int(rng.integers(0, 8)),
+                   guard=bool(rng.integers(0, 2)))
+
+
+@pytest.mark.parametrize("w", [3, 4, 5])
+def test_bounds_family_bruteforce(w):
+    seen = set()
+    for p in _bounds_params(w, 40, 7 + w):
+        a = queries.bounds_query(**p).to_array()
+        bf, wit = oracle.brute_force(a, max_bits=24)
+        cnf, res = solve_ir(a)
+        assert res["verdict"] == bf, p
+        assert bf == bounds_algebra(**p) == bounds_enum(**p), p
+        if bf == oracle.SAT:
+            assert evaluate(a, wit[:4])
+            assert evaluate(a, model_words(cnf, res["model"]))
+        seen.add(bf)
+    assert seen == {oracle.SAT, oracle.UNSAT}
+
+
+@pytest.mark.parametrize("w", [3, 4, 5])
+def test_partition_family_bruteforce(w):
+    rng = np.random.default_rng(100 + w)
+    seen = set()
+    for _ in range(40):
+        k = int(rng.integers(2, 9))
+        p = dict(w=w, k1=int(rng.integers(1, 5)), k0=int(rng.integers(0, 8)),
+                 a=int(rng.integers(1, 5)), c=int(rng.integers(0, 8)), k=k,
+                 j=int(rng.integers(0, k)), guard=bool(rng.integers(0, 2)))
+        a = queries.partition_query(**p).to_array()
+        bf, wit = oracle.brute_force(a, max_bits=24)
+        cnf, res = solve_ir(a)
+        assert res["verdict"] == bf, p
+        assert bf == partition_algebra(**p) == partition_enum(**p), p
+        if bf == oracle.SAT:
+            assert evaluate(a, model_words(cnf, res["model"]))
+        seen.add(bf)
+    assert seen == {oracle.SAT, oracle.UNSAT}
+
+
+# ---------------------------------------------------------------------------
+# Each encoder gadget against the definition, exhaustively on 3-bit words
+# ---------------------------------------------------------------------------
+
+def _gadget_ir(op, x_w, y_w, target, rel):
+    ir = IR()
+    x = ir.free(x_w)
+    y = ir.free(y_w)
+    if op == "add":
+        r = ir.add(x, y)
+    elif op == "mul":
+        r = ir.mul(x, y)
+    elif op == "div3":
+        r = ir.udiv(x, 3)
+    elif op == "rem5":
+        r = ir.urem(x, 5)
+    elif op == "ult":
+        ir.assert_(ir.ult(x, y) if target else ir.not_(ir.ult(x, y)))
+        return ir
+    elif op == "ule":
+        ir.assert_(ir.ule(x, y) if target else ir.not_(ir.ule(x, y)))
+        return ir
+    t = ir.const(target)
+    ir.assert_(ir.eq(r, t) if rel == "eq" else ir.ult(r, t))
+    return ir
+
+
+@pytest.mark.parametrize("op", ["add", "mul", "div3", "rem5", "ult", "ule"])
+def test_gadgets_exhaustive(op):
+    targets = range(0, 2) if op in ("ult", "ule") else range(0, 52)
+    for target in targets:
+        for rel in (("eq", "lt") if op not in ("ult", "ule") else ("eq",)):
+            ir = _gadget_ir(op, 3, 3, target, rel)
+            a = ir.to_array()
+            bf, _ = oracle.brute_force(a, max_bits=12)
+            cnf, res = solve_ir(a, trace=True)
+            assert res["verdict"] == bf, (op, target, rel)
+            if bf == oracle.UNSAT:
+                assert oracle.rup_check(cnf, res["trace"]) == 1
+            else:
+                assert evaluate(a, model_words(cnf, res["model"]))
+
+
+# ---------------------------------------------------------------------------
+# Closed forms over the full config-1 family and the config-2 generator
+# ---------------------------------------------------------------------------
+
+def test_config1_closed_form_w8():
+    irs, params = queries.config1(256)
+    r = oracle.solve_queries(irs)
+    for i, p in enumerate(params):
+        want = bounds_algebra(**p)
+        assert want == bounds_enum(**p)
+        assert r["verdict"][i] == (oracle.SAT if want else oracle.UNSAT), p
+        if want:
+            assert evaluate(irs[i], r["words"][i][:4])
+    # the spec special case: a = 1, c = 0 with the guard kept is UNSAT,
+    # and without the guard the same query is SAT
+    for k1 in (1, 2, 3, 4):
+        for k0 in (0, 5):
+            g = queries.bounds_query(8, k1, k0, 1, 0, True).to_array()
+            u = queries.bounds_query(8, k1, k0, 1, 0, False).to_array()
+            assert oracle.solve_queries([g, u])["verdict"].tolist() == [oracle.UNSAT, oracle.SAT]
+
+
+@pytest.mark.parametrize("w,count", [(8, 4096), (10, 512)])
+def test_config2_closed_form_small_width(w, count):
+    irs, params = queries.config2(count, w=w)
+    r = oracle.solve_queries(irs)
+    for i, p in enumerate(params):
+        want = partition_algebra(**p)
+        if w <= 8 or i < 64:
+            assert want == partition_enum(**p), p
+        assert r["verdict"][i] == (oracle.SAT if want else oracle.UNSAT), p
+        if want:
+            assert evaluate(irs[i], r["words"][i][:4])
+
+
+def test_config2_closed_form_w16_stored():
+    """The stored full-size config-2 oracle verdicts (written by
+    tests/golden/make_oracle_verdicts.py, which calls only the oracle) agree
+    with the closed form on every one of the 4,096 queries."""
+    path = os.path.join(GOLDEN, "config2_w16_oracle_verdicts.txt")
+    stored = np.array([int(x) for x in open(path).read().split()], dtype=np.uint8)
+    _, params = queries.config2(4096)
+    assert len(stored) == 4096
+    want = np.array([oracle.SAT if partition_algebra(**p) else oracle.UNSAT for p in params])
+    assert (stored == want).all()
+
+
+# ---------------------------------------------------------------------------
+# RUP checking of UNSAT refutations, and the checker itself
+# ---------------------------------------------------------------------------
+
+def _cnf_from_3sat(nv, lits):
+    return oracle.CNF(nv, np.arange(0, 3 * len(lits) + 1, 3), lits.reshape(-1))
+
+
+def test_rup_refutations_random_3sat():
+    n_unsat = 0
+    for s in range(40):
+        nv, lits = queries.random_3sat(900 + s, 40, 40, ratio=5.0)
+        cnf = _cnf_from_3sat(nv, lits)
+        res = oracle.dpll(cnf, want_trace=True)
+        if res["verdict"] == oracle.UNSAT:
+            n_unsat += 1
+            assert oracle.rup_check(cnf, res["trace"]) == 1
+            # the checker rejects a trace whose final empty clause is dropped
+            t = res["trace"]
+            assert oracle.rup_check(cnf, t[:-1][: np.flatnonzero(t[:-1] == 0)[-1] + 1]) == 0
+        else:
+            assert cnf_satisfied(cnf.clause_begin, cnf.lits, res["model"])
+    assert n_unsat >= 10
+
+
+def test_rup_checker_rejects_non_implied_clause():
+    # all four 2-clauses over x1, x2 (UNSAT); x3 does not occur
+    cnf = oracle.CNF(3, [0, 2, 4, 6, 8], [1, 2, -1, 2, 1, -2, -1, -2])
+    assert oracle.rup_check(cnf, np.array([2, 0, 0], np.int32)) == 1
+    assert oracle.rup_check(cnf, np.array([3, 0, 0], np.int32)) == 0   # (x3) is not RUP
+    assert oracle.rup_check(cnf, np.array([2, 0], np.int32)) == 0      # no empty clause
+    sat = oracle.CNF(2, [0, 2, 4], [1, 2, -1, 2])
+    assert oracle.rup_check(sat, np.array([2, 0, 0], np.int32)) == 0   # formula is SAT
+
+
+# ---------------------------------------------------------------------------
+# Random 3-SAT against brute force over all 2^n assignments
+# ---------------------------------------------------------------------------
+
+def _bf_3sat(nv, lits):
+    a = np.arange(1 << nv, dtype=np.uint32)
+    ok = np.ones(1 << nv, dtype=bool)
+    for cl in lits:
+        sat = np.zeros(1 << nv, dtype=bool)
+        for l in cl:
+            bit = (a >> (abs(int(l)) - 1)) & 1
+            sat |= (bit == 1) if l > 0 else (bit == 0)
+        ok &= sat
+    return bool(ok.any())
+
+
+def test_random_3sat_bruteforce():
+    seen = set()
+    for s in range(60):
+        nv, lits = queries.random_3sat(77 + s, 10, 14)
+        cnf = _cnf_from_3sat(nv, lits)
+        res = oracle.dpll(cnf)
+        want = _bf_3sat(nv, lits)
+        assert res["verdict"] == (oracle.SAT if want else oracle.UNSAT)
+        if want:
+            assert cnf_satisfied(cnf.clause_begin, cnf.lits, res["model"])
+        seen.add(want)
+    assert seen == {True, False}
+
+
+def test_degenerate_cnfs():
+    empty_formula = oracle.CNF(3, [0], [])
+    r = oracle.dpll(empty_formula)
+    assert r["verdict"] == oracle.SAT
+    empty_clause = oracle.CNF(2, [0, 1, 1], [1])
+    assert oracle.dpll(empty_clause)["verdict"] == oracle.UNSAT
+    contradict = oracle.CNF(1, [0, 1, 2], [1, -1])
+    assert oracle.dpll(contradict)["verdict"] == oracle.UNSAT
+    dup = oracle.CNF(2, [0, 3, 4], [1, 1, 2, -2])   # (x1|x1|x2) & -x2 -> x1
+    r = oracle.dpll(dup)
+    assert r["verdict"] == oracle.SAT and r["model"].tolist() == [1, 0]
+
+
+def test_budget_gives_unknown():
+    nv, lits = queries.random_3sat(4242, 150, 150)
+    r = oracle.dpll(_cnf_from_3sat(nv, lits), budget=5)
+    assert r["verdict"] == oracle.UNKNOWN and r["decisions"] == 5
