@@ -1,0 +1,205 @@
+/*
+ * scuba.h -- C ABI of libscuba: batched satisfiability checks for
+ * out-of-bounds queries on a GB300 (sm_103a).
+ *
+ * The paper decides, for every static memory instruction of a CUDA kernel,
+ * whether the three kinds of constraints of Sec. V-B can hold simultaneously
+ * under some program input (kind 1: thread/block ids below their dimensions;
+ * kind 2: the offset reaches the allocation size, or leaves its logical
+ * partition of Sec. IV-B / Fig. 7b; kind 3: equalities defining offset, size,
+ * grid dimensions and asserts). SAT means an OOB is possible (Sec. V-B, step
+ * 10). This library bit-blasts each query to CNF on the host and decides
+ * whole batches of CNFs with a complete DPLL on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SCUBA_OK (0) or a negative scuba_status. Argument errors
+ *     are detected synchronously; device-side errors (malformed literals,
+ *     timeouts) are reported by scuba_sync_status() on the same stream.
+ *   - Ownership: the caller owns every buffer it passes (inputs, verdicts,
+ *     models, stats). The library owns only its scratch memory, cached per
+ *     device; scuba_release() frees it.
+ *   - Streams: `stream` is a cudaStream_t passed as void*; NULL means the
+ *     legacy default stream. Device entry points are asynchronous on it.
+ *   - Literals at the boundary are DIMACS: +v / -v with v in 1..num_vars of
+ *     the instance, no 0 terminators (clause_begin delimits clauses).
+ *   - A batch with an empty clause in an instance gives that instance UNSAT;
+ *     an instance with no clauses is SAT (model all 0).
+ *   - Not thread-safe: calls on one device must not overlap from several host
+ *     threads.
+ */
+#ifndef SCUBA_H
+#define SCUBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Verdict values written to the uint8 verdict array. */
+enum { SCUBA_UNSAT = 0, SCUBA_SAT = 1, SCUBA_UNKNOWN = 2 };
+
+/* Status codes (negative) returned by every entry point. */
+enum {
+  SCUBA_OK = 0,
+  SCUBA_ERR_ARG = -1,       /* NULL pointer, negative size, bad option */
+  SCUBA_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+  SCUBA_ERR_NOMEM = -3,     /* scratch allocation failed */
+  SCUBA_ERR_TIMEOUT = -4,   /* time budget reached; unfinished instances UNKNOWN */
+  SCUBA_ERR_MALFORMED = -5, /* literal 0 or |literal| > num_vars, bad offsets */
+  SCUBA_ERR_ABORTED = -6,   /* the caller's abort flag was raised */
+  SCUBA_ERR_TOO_LARGE = -7  /* an instance exceeds the solver's size limits */
+};
+
+/* Branching heuristics (Sec. VIII-style extensions are not in the paper; the
+   paper's solver is a CPU CP-SAT call, Sec. V-B step 10). */
+enum { SCUBA_HEUR_ACTIVITY = 0, SCUBA_HEUR_LEARNED = 1 };
+
+/*
+ * A batch of CNF instances in CSR form. Array pointers are DEVICE pointers
+ * (owned by the caller) unless stated otherwise.
+ *   inst_clause_begin [num_instances+1]  clause index range of instance i
+ *   clause_begin      [total_clauses+1]  literal index range of clause c
+ *                                        (global indices into lits)
+ *   lits              [total_lits]       DIMACS literals (+-v), int32
+ *   inst_num_vars     [num_instances]    variables of instance i (>= 0)
+ *   inst_var_begin    [num_instances+1]  offset of instance i in model[]
+ * Host-side sizes (plain values, used to size scratch without a device sync):
+ *   total_clauses, total_lits = inst_clause_begin[n], clause_begin[total_clauses]
+ *   total_vars = inst_var_begin[n], max_vars = max_i inst_num_vars[i]
+ */
+typedef struct scuba_cnf_batch {
+  int32_t num_instances;
+  int32_t max_vars;
+  int64_t total_clauses;
+  int64_t total_lits;
+  int64_t total_vars;
+  const int64_t* inst_clause_begin;
+  const int64_t* clause_begin;
+  const int32_t* lits;
+  const int32_t* inst_num_vars;
+  const int64_t* inst_var_begin;
+} scuba_cnf_batch;
+
+/* Options for scuba_solve_batch_ex. Initialise with scuba_options_init(). */
+typedef struct scuba_options {
+  int32_t heuristic;         /* SCUBA_HEUR_ACTIVITY or SCUBA_HEUR_LEARNED */
+  int32_t learned_depth;     /* LEARNED: decisions at depth < learned_depth use the MLP */
+  const void* mlp_weights;   /* LEARNED: device pointer, layout of scuba_mlp_layout() */
+  int64_t decision_budget;   /* per instance (all its subtrees); <= 0: unlimited */
+  int64_t time_budget_ms;    /* whole call; <= 0: 600000 */
+  int32_t split;             /* 1: hand DPLL subtrees of busy instances to idle warps */
+  int32_t warps_per_block;   /* 0: autotuned default */
+  int32_t blocks_per_sm;     /* 0: autotuned default */
+  int32_t split_interval;    /* decisions between checks for idle warps; 0: default */
+  int64_t* stats;            /* device [num_instances*SCUBA_NSTATS], added to; may
+                                be NULL. Per instance: decisions, conflicts,
+                                propagations (trail literals processed),
+                                occurrence entries visited, activity entries read
+                                by decisions, trail entries undone by backtracks */
+  const int32_t* order;      /* device [num_instances]: processing order; may be NULL */
+  const volatile int32_t* abort_flag; /* host-mapped or device flag; nonzero stops
+                                          the solve (SCUBA_ERR_ABORTED); may be NULL */
+  void* search_event_begin;  /* cudaEvent_t recorded on `stream` right before the
+                                search kernel launch; may be NULL */
+  void* search_event_end;    /* cudaEvent_t recorded right after it; may be NULL */
+} scuba_options;
+
+/* Number of int64 counters per instance in scuba_options.stats. */
+#define SCUBA_NSTATS 6
+
+/* Fills `opt` with defaults (activity branching, splitting on, no budgets). */
+int scuba_options_init(scuba_options* opt);
+
+/*
+ * Decide every instance of the batch (Sec. V-B step 10, one query per static
+ * memory instruction, Sec. V-B). verdict: device uint8[num_instances].
+ * model: device uint8[inst_var_begin[n]] receiving 0/1 per variable of every
+ * SAT instance (untouched for UNSAT/UNKNOWN), or NULL.
+ * Search: complete DPLL -- unit propagation over occurrence lists, activity
+ * branching with false polarity first, chronological backtracking.
+ */
+int scuba_solve_batch(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t* model,
+                      void* stream);
+int scuba_solve_batch_ex(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t* model,
+                         void* stream, const scuba_options* opt);
+
+/*
+ * Same as scuba_solve_batch_ex, but every array of `batch`, `verdict`,
+ * `model` and `opt->stats` is a HOST pointer. The call copies the batch to
+ * library scratch on the device, solves, copies verdicts/models/stats back
+ * and synchronises the stream before returning. Returns the solve status.
+ */
+int scuba_solve_batch_host(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t* model,
+                           void* stream, const scuba_options* opt);
+
+/* Waits for `stream` and returns the status of the last solve issued on it. */
+int scuba_sync_status(void* stream);
+
+/* Frees the library's cached device scratch on the current device. */
+void scuba_release(void);
+
+/* Thread-local message describing the last error. */
+const char* scuba_last_error(void);
+
+/* Library ABI version (monotonic integer). */
+int scuba_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Host side: query encoding and model re-verification                        */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Serialized query IR (int64 array, layout documented in workloads/ir.py):
+ * expression-tree nodes of Sec. V-A (FREE input words, constants, +, *, /k,
+ * %k) and Boolean nodes (<, <=, ==, or, and, not), plus the asserted roots
+ * (the kind 1/2/3 constraints of Sec. V-B).
+ */
+typedef struct scuba_encoded scuba_encoded; /* opaque host handle */
+
+/*
+ * Bit-blasts n queries on `nthreads` host threads (<= 0: all cores) into
+ * 3-CNF. irs + ir_offsets[n+1] hold the serialized queries (host memory).
+ * On success *out owns the encoded batch.
+ */
+int scuba_encode_batch(int32_t n, const int64_t* irs, const int64_t* ir_offsets,
+                       int32_t nthreads, scuba_encoded** out);
+
+/* sizes[6] = {num_instances, total_clauses, total_lits, total_vars, max_vars,
+   total_input_bits}. */
+int scuba_encoded_sizes(const scuba_encoded* enc, int64_t* sizes);
+
+/* Copies the CSR of an encoded batch into caller HOST arrays sized by
+   scuba_encoded_sizes: inst_clause_begin[n+1], clause_begin[C+1], lits[L],
+   inst_num_vars[n], inst_var_begin[n+1]. */
+int scuba_encoded_copy(const scuba_encoded* enc, int64_t* inst_clause_begin,
+                       int64_t* clause_begin, int32_t* lits, int32_t* inst_num_vars,
+                       int64_t* inst_var_begin);
+
+/* Input-word map: inst_input_begin[n+1] into input_width[] (one entry per
+   FREE word), and for each input bit its CNF variable (LSB first) in
+   input_var[total_input_bits], bits of word k of instance i starting at
+   the running sum of widths. */
+int scuba_encoded_inputs(const scuba_encoded* enc, int64_t* inst_input_begin,
+                         int32_t* input_width, int32_t* input_var);
+
+void scuba_encoded_free(scuba_encoded* enc);
+
+/*
+ * Re-verifies every SAT verdict on the host: decodes the input words of the
+ * instance from `model` (host, as written by the solver) through the input
+ * map and evaluates the ORIGINAL integer constraints of the query exactly
+ * (arbitrary precision). ok[i] = 1 verified, 0 model violates a constraint,
+ * 2 not SAT (nothing to check). Returns the number of failures (>= 0) or a
+ * negative status.
+ */
+int scuba_verify_batch(const scuba_encoded* enc, const int64_t* irs, const int64_t* ir_offsets,
+                       const uint8_t* verdict, const uint8_t* model, int32_t nthreads,
+                       uint8_t* ok);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCUBA_H */

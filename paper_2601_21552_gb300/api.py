@@ -1,0 +1,108 @@
+"""Torch-facing convenience layer over the C ABI.
+
+torch provides device memory and streams only; encoding, solving and
+verification all happen in libscuba. The functions here marshal tensors into
+the ``scuba_cnf_batch`` / ``scuba_options`` structs and call the ABI.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class DeviceBatch:
+    """The CSR of an encoded batch resident on a CUDA device (torch tensors)."""
+
+    def __init__(self, enc: B.Encoded, device: str | torch.device = "cuda", pin: bool = True):
+        self.enc = enc
+        self.n = enc.n
+        self.max_vars = enc.max_vars
+        self.total_clauses = enc.total_clauses
+        self.total_lits = enc.total_lits
+        self.total_vars = enc.total_vars
+        dev = torch.device(device)
+
+        def up(a: np.ndarray) -> torch.Tensor:
+            t = torch.from_numpy(np.ascontiguousarray(a))
+            if pin:
+                t = t.pin_memory()
+            return t.to(dev, non_blocking=True)
+
+        self.icb = up(enc.inst_clause_begin)
+        self.cb = up(enc.clause_begin)
+        self.lits = up(enc.lits if len(enc.lits) else np.zeros(1, np.int32))
+        self.nv = up(enc.inst_num_vars if self.n else np.zeros(1, np.int32))
+        self.vb = up(enc.inst_var_begin)
+        self.h2d_bytes = sum(int(x.nbytes) for x in (enc.inst_clause_begin, enc.clause_begin,
+                                                       enc.lits, enc.inst_num_vars,
+                                                       enc.inst_var_begin))
+
+    def struct(self) -> B.scuba_cnf_batch:
+        return B.make_batch(self.n, self.max_vars, self.total_clauses, self.total_lits,
+                            self.total_vars, self.icb.data_ptr(), self.cb.data_ptr(),
+                            self.lits.data_ptr(), self.nv.data_ptr(), self.vb.data_ptr())
+
+
+def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
+            time_budget_ms: int = 0, split: bool = True, warps_per_block: int = 0,
+            blocks_per_sm: int = 0, split_interval: int = 0, stats: torch.Tensor | None = None,
+            order: torch.Tensor | None = None, mlp_weights: torch.Tensor | None = None,
+            learned_depth: int = 0, abort_flag_ptr: int | None = None,
+            events: tuple | None = None) -> B.scuba_options:
+    o = B.scuba_options_init()
+    o.heuristic = heuristic
+    o.decision_budget = decision_budget
+    o.time_budget_ms = time_budget_ms
+    o.split = 1 if split else 0
+    o.warps_per_block = warps_per_block
+    o.blocks_per_sm = blocks_per_sm
+    o.split_interval = split_interval
+    o.stats = stats.data_ptr() if stats is not None else None
+    o.order = order.data_ptr() if order is not None else None
+    o.mlp_weights = mlp_weights.data_ptr() if mlp_weights is not None else None
+    o.learned_depth = learned_depth
+    o.abort_flag = abort_flag_ptr
+    if events is not None:
+        o.search_event_begin = events[0].cuda_event
+        o.search_event_end = events[1].cuda_event
+    return o
+
+
+def solve(db: DeviceBatch, want_model: bool = True, stats: bool = True,
+          stream: torch.cuda.Stream | None = None, **opts):
+    """Launch scuba_solve_batch_ex on `stream` (torch's current stream by
+    default) and return (verdict u8[n], model u8[total_vars] | None,
+    stats i64[n,3] | None) device tensors. Asynchronous: call
+    ``status(stream)`` to wait and collect the device status."""
+    dev = db.icb.device
+    verdict = torch.empty(max(db.n, 1), dtype=torch.uint8, device=dev)
+    model = torch.zeros(max(db.total_vars, 1), dtype=torch.uint8, device=dev) if want_model else None
+    st = torch.zeros((max(db.n, 1), B.SCUBA_NSTATS), dtype=torch.int64, device=dev) if stats else None
+    o = options(stats=st, **opts)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    B.scuba_solve_batch_ex(db.struct(), verdict.data_ptr(),
+                           model.data_ptr() if model is not None else None,
+                           s.cuda_stream, o)
+    return verdict[:db.n], (model[:db.total_vars] if model is not None else None), \
+        (st[:db.n] if st is not None else None)
+
+
+def status(stream: torch.cuda.Stream | None = None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return B.scuba_sync_status(s.cuda_stream)
+
+
+def solve_queries(irs: list, device: str = "cuda", **opts):
+    """Encode on the host, upload, solve, re-verify every SAT model on the
+    host. Returns dict(verdict, stats, verified, enc)."""
+    enc = B.scuba_encode_batch(irs)
+    db = DeviceBatch(enc, device)
+    v, m, st = solve(db, **opts)
+    rc = status()
+    vh = v.cpu().numpy()
+    mh = m.cpu().numpy() if m is not None else np.zeros(1, np.uint8)
+    fails, ok = B.scuba_verify_batch(enc, vh, mh)
+    return dict(verdict=vh, stats=st.cpu().numpy() if st is not None else None,
+                verified=ok, fails=fails, status=rc, enc=enc, model=mh)

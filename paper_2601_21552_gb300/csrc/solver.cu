@@ -1,0 +1,1285 @@
+// solver.cu -- GPU DPLL over batches of CNFs (the satisfiability step of
+// Sec. V-B, step 10, applied to one query per static memory instruction).
+//
+// Layout in HBM (per batch, built by the prep kernels from the caller's CSR):
+//   norm[L]        u32  normalised literal code per literal slot (2(v-1)+neg),
+//                       NONE for dropped slots, UNIT_BIT for unit clauses
+//   occ_begin[..]  u32  per instance 2V+1 offsets: occurrence list of each
+//                       literal code (clauses that contain it)
+//   ent[L]         u64  occurrence entries, in clause order within a list:
+//                       binary (x|y) in x's list = {y, NONE}; ternary
+//                       (x|y|z) in x's list = {y, z}; longer clauses =
+//                       {LONG_CLAUSE|local clause index, 0}
+//   units[C]       u32  unit-clause literal codes, compacted per instance
+// Per worker slot (one warp): trail[Vmax], dstack[Vmax], act[Vmax] in global
+// memory; the assignment (2 bits per variable) in shared memory.
+//
+// Search per instance (complete DPLL): unit propagation to a fixpoint over
+// occurrence lists, frontier-parallel across the 32 lanes; on conflict bump
+// the activity of the falsified clause's variables and backtrack
+// chronologically to the deepest decision not yet flipped; otherwise decide
+// the unassigned variable of highest activity (ties: lowest id), value false
+// first. A busy warp hands the untried branch of its shallowest open decision
+// to an idle warp (subtree splitting) so that hard instances spread over the
+// whole GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/scuba.h"
+#include "scuba_internal.h"
+
+namespace scuba {
+namespace dev {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr uint32_t NONE = 0xffffffffu;
+constexpr uint32_t LONG_CLAUSE = 0x80000000u;
+constexpr uint32_t UNIT_BIT = 0x40000000u;
+constexpr uint32_t FLIP = 0x80000000u;
+constexpr uint32_t F_EMPTY = 1u, F_BAD = 2u;
+constexpr int MAX_PREFIX = 248;   // literals in a split job's prefix
+
+__device__ __forceinline__ uint32_t code_of(int32_t l) {
+  int32_t v = l > 0 ? l : -l;
+  return 2u * (uint32_t)(v - 1) + (l < 0 ? 1u : 0u);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// --------------------------------------------------------------------------
+// Prep
+// --------------------------------------------------------------------------
+
+struct Ctrl {
+  uint32_t next_inst;   // fresh-instance counter
+  uint32_t inst_left;   // instances not finished yet
+  uint32_t idle;        // warps waiting for work
+  int32_t status;       // first error (scuba status code)
+  uint32_t q_head, q_tail;
+  uint64_t t0;          // globaltimer at launch
+  uint32_t jobs_split;  // statistics
+  uint32_t pad;
+};
+
+__device__ void fail_batch(Ctrl* c, int32_t st) { atomicCAS(&c->status, 0, st); }
+
+__device__ __forceinline__ bool batch_failed(Ctrl* c) {
+  return *(volatile int32_t*)&c->status != 0;
+}
+
+struct Prep {
+  int n;
+  int64_t C, L;
+  int64_t total_vars;  // model size promised by the caller
+  int64_t occ_cap;     // allocated occurrence-offset entries
+  int32_t vmax;
+  const int64_t* vb;
+  Ctrl* ctrl;
+  const int64_t* icb;
+  const int64_t* cb;
+  const int32_t* lits;
+  const int32_t* nv;
+  int64_t* occ_base;   // [n+1]
+  uint32_t* norm;      // [L]
+  uint32_t* occ_cnt;   // [occ_total] counts, then fill cursors
+  uint32_t* occ_begin; // [occ_total]
+  uint64_t* ent;       // [L]
+  uint32_t* units;     // [C]
+  uint32_t* nunits;    // [n]
+  uint32_t* flags;     // [n]
+};
+
+__device__ __forceinline__ int32_t clamp_nv(int32_t v, int32_t vmax) {
+  return v < 0 ? 0 : (v > vmax ? vmax : v);
+}
+
+// occ_base[i] = sum_{j<i} (2 nv[j] + 1); single block, chunked scan. Also
+// validates the batch header: clause ranges monotonic and covering exactly
+// [0, total_clauses), 0 <= nv <= max_vars, model ranges inside total_vars.
+// Instances that fail get F_BAD; a header that cannot be trusted at all
+// stops the whole batch with SCUBA_ERR_MALFORMED.
+__global__ void k_occ_base(Prep P) {
+  __shared__ int64_t part[1024];
+  __shared__ int bad_header;
+  const int n = P.n, t = threadIdx.x, T = blockDim.x;
+  if (t == 0) bad_header = (P.icb[0] != 0 || P.icb[n] != P.C);
+  __syncthreads();
+  const int per = (n + T - 1) / T;
+  const int b = min(n, t * per), e = min(n, b + per);
+  int64_t s = 0;
+  for (int i = b; i < e; i++) {
+    const int32_t v = P.nv[i];
+    if (P.icb[i] > P.icb[i + 1]) bad_header = 1;
+    uint32_t f = 0;
+    if (v < 0 || v > P.vmax) f |= F_BAD;
+    if (P.vb[i] < 0 || P.vb[i] + (int64_t)(v < 0 ? 0 : v) > P.total_vars) f |= F_BAD;
+    if (f) atomicOr(&P.flags[i], f);
+    s += 2 * (int64_t)clamp_nv(v, P.vmax) + 1;
+  }
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int64_t acc = 0;
+    for (int k = 0; k < T; k++) {
+      int64_t v = part[k];
+      part[k] = acc;
+      acc += v;
+    }
+    P.occ_base[n] = acc;
+    if (acc > P.occ_cap) bad_header = 1;
+  }
+  __syncthreads();
+  int64_t acc = part[t];
+  for (int i = b; i < e; i++) {
+    P.occ_base[i] = acc;
+    acc += 2 * (int64_t)clamp_nv(P.nv[i], P.vmax) + 1;
+  }
+  if (t == 0 && bad_header) fail_batch(P.ctrl, SCUBA_ERR_MALFORMED);
+}
+
+__device__ __forceinline__ int find_inst(const int64_t* icb, int n, int64_t c) {
+  int lo = 0, hi = n - 1;  // largest i with icb[i] <= c
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (icb[mid] <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One thread per clause: validate, normalise clauses of length <= 3
+// (duplicates removed, tautologies dropped), count occurrences.
+__global__ void k_normalize(Prep P) {
+  if (batch_failed(P.ctrl)) return;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < P.C;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int i = find_inst(P.icb, P.n, c);
+    while (i + 1 < P.n && P.icb[i + 1] <= c) i++;  // skip empty instances
+    const int V = clamp_nv(P.nv[i], P.vmax);
+    const int64_t b = P.cb[c], e = P.cb[c + 1];
+    if (b < 0 || e < b || e > P.L) { atomicOr(&P.flags[i], F_BAD); continue; }
+    const int64_t len = e - b;
+    bool bad = false;
+    for (int64_t k = b; k < e; k++) {
+      int32_t l = P.lits[k];
+      if (l == 0 || l > V || l < -V) bad = true;
+    }
+    if (bad) {
+      atomicOr(&P.flags[i], F_BAD);
+      for (int64_t k = b; k < e; k++) P.norm[k] = NONE;
+      continue;
+    }
+    if (len == 0) { atomicOr(&P.flags[i], F_EMPTY); continue; }
+    uint32_t* cnt = P.occ_cnt + P.occ_base[i];
+    if (len <= 3) {
+      uint32_t u[3];
+      int k = 0;
+      bool taut = false;
+      for (int64_t q = b; q < e; q++) {
+        uint32_t x = code_of(P.lits[q]);
+        bool dup = false;
+        for (int r = 0; r < k; r++) {
+          if (u[r] == x) dup = true;
+          if (u[r] == (x ^ 1u)) taut = true;
+        }
+        P.norm[q] = dup ? NONE : x;
+        if (!dup) u[k++] = x;
+      }
+      if (taut) {
+        for (int64_t q = b; q < e; q++) P.norm[q] = NONE;
+      } else if (k == 1) {
+        for (int64_t q = b; q < e; q++)
+          if (P.norm[q] != NONE) P.norm[q] |= UNIT_BIT;
+      } else {
+        for (int r = 0; r < k; r++) atomicAdd(&cnt[u[r]], 1u);
+      }
+    } else {
+      for (int64_t q = b; q < e; q++) {
+        uint32_t x = code_of(P.lits[q]);
+        P.norm[q] = x;
+        atomicAdd(&cnt[x], 1u);
+      }
+    }
+  }
+}
+
+// One warp per instance: exclusive scan of the 2V counts -> occ_begin; the
+// counts become fill cursors.
+__global__ void k_occ_scan(Prep P) {
+  if (batch_failed(P.ctrl)) return;
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  for (int i = w; i < P.n; i += W) {
+    const int64_t base = P.occ_base[i];
+    const uint32_t m = 2u * (uint32_t)clamp_nv(P.nv[i], P.vmax);
+    uint32_t run = 0;
+    for (uint32_t s = 0; s < m; s += 32) {
+      uint32_t k = s + lane;
+      uint32_t v = k < m ? P.occ_cnt[base + k] : 0u;
+      uint32_t inc = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, inc, d);
+        if (lane >= d) inc += y;
+      }
+      if (k < m) {
+        P.occ_begin[base + k] = run + inc - v;
+        P.occ_cnt[base + k] = run + inc - v;
+      }
+      run += __shfl_sync(FULL, inc, 31);
+    }
+    if (lane == 0) P.occ_begin[base + m] = run;
+  }
+}
+
+// One warp per instance: fill occurrence entries in clause order
+// (deterministic), and compact the unit literals.
+__global__ void k_fill(Prep P) {
+  if (batch_failed(P.ctrl)) return;
+  __shared__ uint32_t sbase[32 * 8];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  uint32_t* my_base = sbase + 32 * wib;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  for (int i = w; i < P.n; i += W) {
+    if (P.flags[i] & F_BAD) continue;
+    const int64_t c0 = P.icb[i], c1 = P.icb[i + 1];
+    const int64_t lbase = c0 < c1 ? P.cb[c0] : 0;
+    uint32_t* cur = P.occ_cnt + P.occ_base[i];
+    uint32_t nunit = 0;
+    for (int64_t cs = c0; cs < c1; cs += 32) {
+      const int64_t c = cs + lane;
+      const bool valid = c < c1;
+      int64_t b = 0, e = 0;
+      uint32_t lits3[3] = {NONE, NONE, NONE};
+      int nk = 0;
+      bool is_long = false, is_unit = false;
+      uint32_t unit_code = 0;
+      if (valid) {
+        b = P.cb[c];
+        e = P.cb[c + 1];
+        if (e - b > 3) {
+          is_long = true;
+          nk = (int)(e - b);
+        } else {
+          for (int64_t q = b; q < e; q++) {
+            uint32_t x = P.norm[q];
+            if (x == NONE) continue;
+            if (x & UNIT_BIT) { is_unit = true; unit_code = x & ~UNIT_BIT; continue; }
+            lits3[nk++] = x;
+          }
+          if (nk < 2) nk = 0;
+        }
+      }
+      // units, in clause order
+      uint32_t ub = __ballot_sync(FULL, is_unit);
+      if (is_unit) P.units[c0 + nunit + __popc(ub & ((1u << lane) - 1u))] = unit_code;
+      nunit += __popc(ub);
+      int rounds = __reduce_max_sync(FULL, (unsigned)nk);
+      for (int k = 0; k < rounds; k++) {
+        const bool has = k < nk;
+        uint32_t code = 0x80000000u | (uint32_t)lane;  // unique dummy
+        uint64_t entry = 0;
+        if (has) {
+          if (is_long) {
+            code = P.norm[b + k];
+            entry = (uint64_t)(LONG_CLAUSE | (uint32_t)(c - c0));
+          } else {
+            code = lits3[k];
+            uint32_t o1 = lits3[k == 0 ? 1 : 0];
+            uint32_t o2 = nk == 3 ? lits3[k == 2 ? 1 : 2] : NONE;
+            entry = (uint64_t)o1 | ((uint64_t)o2 << 32);
+          }
+        }
+        uint32_t grp = __match_any_sync(FULL, code);
+        int leader = __ffs(grp) - 1;
+        if (has && lane == leader) {
+          my_base[lane] = cur[code];
+          cur[code] += __popc(grp);
+        }
+        __syncwarp();
+        if (has) {
+          uint32_t pos = my_base[leader] + __popc(grp & ((1u << lane) - 1u));
+          P.ent[lbase + pos] = entry;
+        }
+        __syncwarp();
+      }
+    }
+    if (lane == 0) P.nunits[i] = nunit;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Solve
+// --------------------------------------------------------------------------
+
+struct Job {            // a DPLL subtree: the instance plus assumed literals
+  int32_t inst;
+  int32_t len;
+  uint32_t lit[MAX_PREFIX];
+  uint32_t seq;         // ring-buffer sequence number (Vyukov MPMC queue)
+  uint32_t pad[1];
+};
+
+struct Solve {
+  int n;
+  int32_t vmax;
+  uint32_t assign_words;   // per-warp shared words (2 bits per variable)
+  const int64_t* icb;
+  const int64_t* cb;
+  const int32_t* lits;
+  const int32_t* nv;
+  const int64_t* vb;
+  const int64_t* occ_base;
+  const uint32_t* occ_begin;
+  const uint64_t* ent;
+  const uint32_t* units;
+  const uint32_t* nunits;
+  const uint32_t* flags;
+  const int32_t* order;
+  uint8_t* verdict;
+  uint8_t* model;
+  int64_t* stats;
+  // per instance bookkeeping
+  uint32_t* pending;       // open jobs of an instance
+  uint32_t* done;          // 1 once the verdict is final
+  unsigned long long* inst_dec;  // decisions so far (budget)
+  // per slot
+  uint32_t* trail;
+  uint32_t* dstack;
+  float* act;
+  // job ring
+  Job* ring;
+  uint32_t ring_cap;       // power of two
+  Ctrl* ctrl;
+  int64_t budget;
+  uint64_t time_ns;
+  const volatile int32_t* abort_flag;
+  int split;
+  int split_interval;
+};
+
+struct WarpShared {
+  uint32_t tail;
+  uint32_t conflict;
+  uint32_t cl[3];
+  uint32_t pad[3];
+};
+
+enum : uint32_t { LV_U = 0, LV_T = 1, LV_F = 2, LV_X = 3 };
+
+__device__ __forceinline__ uint32_t lit_value(const uint32_t* asg, uint32_t l) {
+  uint32_t v = l >> 1;
+  uint32_t bits = (asg[v >> 4] >> ((v & 15u) * 2u)) & 3u;
+  if (bits == 0u || bits == 3u) return bits == 0u ? LV_U : LV_X;
+  // bits 1 = variable true, 2 = variable false
+  bool lit_true = (bits == 1u) ^ ((l & 1u) != 0u);
+  return lit_true ? LV_T : LV_F;
+}
+
+struct Warp {
+  const Solve* S;
+  uint32_t* asg;
+  WarpShared* ws;
+  uint32_t* trail;
+  uint32_t* dstack;
+  float* act;
+  int lane;
+  int inst;
+  uint32_t V;
+  const uint32_t* occ;
+  const uint64_t* ent;
+  int64_t c0;
+  uint32_t head;
+  uint32_t nd;
+  uint32_t nd_fixed;       // decisions below this index are assumptions
+  float inc;
+  int64_t decisions, conflicts, props, visits, act_reads, undone;
+};
+
+__device__ __forceinline__ void record_conflict(Warp& w, uint32_t a, uint32_t b, uint32_t c) {
+  if (atomicCAS(&w.ws->conflict, 0u, 1u) == 0u) {
+    w.ws->cl[0] = a;
+    w.ws->cl[1] = b;
+    w.ws->cl[2] = c;
+  }
+}
+
+// Assign literal l true. Returns false on a clash with the opposite value.
+__device__ __forceinline__ bool imply(Warp& w, uint32_t l) {
+  uint32_t v = l >> 1;
+  uint32_t sh = (v & 15u) * 2u;
+  uint32_t mask = ((l & 1u) ? 2u : 1u) << sh;
+  uint32_t old = atomicOr(&w.asg[v >> 4], mask);
+  uint32_t ob = (old >> sh) & 3u;
+  if (ob == 0u) {
+    uint32_t pos = atomicAdd(&w.ws->tail, 1u);
+    w.trail[pos] = l;
+    return true;
+  }
+  if (ob == (mask >> sh)) return true;
+  if ((old & mask) == 0u) atomicAnd(&w.asg[v >> 4], ~mask);  // undo our bit
+  return false;
+}
+
+__device__ void eval_long(Warp& w, uint32_t local, uint32_t f) {
+  const int64_t c = w.c0 + local;
+  const int64_t b = w.S->cb[c], e = w.S->cb[c + 1];
+  uint32_t open_lit = NONE;
+  int n_open = 0;
+  for (int64_t q = b; q < e; q++) {
+    uint32_t x = code_of(__ldg(&w.S->lits[q]));
+    uint32_t vx = lit_value(w.asg, x);
+    if (vx == LV_T || vx == LV_X) return;
+    if (vx == LV_U && x != open_lit) {
+      n_open++;
+      open_lit = x;
+      if (n_open > 1) return;
+    }
+  }
+  if (n_open == 0) {
+    record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
+  } else if (!imply(w, open_lit)) {
+    record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
+  }
+}
+
+// Visit one occurrence entry of the falsified literal f.
+__device__ __forceinline__ void eval_entry(Warp& w, uint32_t f, uint64_t e) {
+  const uint32_t a = (uint32_t)e, b = (uint32_t)(e >> 32);
+  if (a & LONG_CLAUSE) {
+    eval_long(w, a & ~LONG_CLAUSE, f);
+    return;
+  }
+  const uint32_t va = lit_value(w.asg, a);
+  if (b == NONE) {  // binary (f | a)
+    if (va == LV_T || va == LV_X) return;
+    if (va == LV_F || !imply(w, a)) record_conflict(w, f, a, NONE);
+    return;
+  }
+  const uint32_t vb = lit_value(w.asg, b);  // ternary (f | a | b)
+  if (va == LV_T || vb == LV_T || va == LV_X || vb == LV_X) return;
+  if (va == LV_F && vb == LV_F) {
+    record_conflict(w, f, a, b);
+  } else if (va == LV_F) {
+    if (!imply(w, b)) record_conflict(w, f, a, b);
+  } else if (vb == LV_F) {
+    if (!imply(w, a)) record_conflict(w, f, a, b);
+  }
+}
+
+// Unit propagation to a fixpoint. Returns true on conflict.
+__device__ bool bcp(Warp& w) {
+  for (;;) {
+    __syncwarp();
+    const uint32_t hi = *(volatile uint32_t*)&w.ws->tail;
+    if (w.head >= hi) return false;
+    const uint32_t lo = w.head;
+    w.head = hi;
+    w.props += hi - lo;
+    for (uint32_t base = lo; base < hi; base += 32) {
+      const uint32_t t = base + w.lane;
+      uint32_t f = 0, beg = 0, cnt = 0;
+      if (t < hi) {
+        f = w.trail[t] ^ 1u;              // the literal that became false
+        beg = __ldg(&w.occ[f]);
+        cnt = __ldg(&w.occ[f + 1]) - beg;
+      }
+      uint32_t inc = cnt;
+      for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, inc, d);
+        if (w.lane >= d) inc += y;
+      }
+      const uint32_t total = __shfl_sync(FULL, inc, 31);
+      w.visits += total;
+      for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+        const uint32_t e = e0 + w.lane;
+        // owner = smallest lane j with inc_j > e
+        int lo_j = 0, hi_j = 31;
+#pragma unroll
+        for (int s = 0; s < 5; s++) {
+          int mid = (lo_j + hi_j) >> 1;
+          uint32_t v = __shfl_sync(FULL, inc, mid);
+          if (v > e) hi_j = mid; else lo_j = mid + 1;
+          if (lo_j > hi_j) lo_j = hi_j;
+        }
+        const int j = lo_j;
+        const uint32_t jinc = __shfl_sync(FULL, inc, j);
+        const uint32_t jcnt = __shfl_sync(FULL, cnt, j);
+        const uint32_t jbeg = __shfl_sync(FULL, beg, j);
+        const uint32_t jf = __shfl_sync(FULL, f, j);
+        if (e < total) {
+          const uint64_t en = __ldg(&w.ent[jbeg + (e - (jinc - jcnt))]);
+          eval_entry(w, jf, en);
+        }
+      }
+      __syncwarp();
+      if (*(volatile uint32_t*)&w.ws->conflict) return true;
+    }
+  }
+}
+
+__device__ void bump(Warp& w) {
+  // activity += inc for the variables of the falsified clause
+  const uint32_t a = w.ws->cl[0], b = w.ws->cl[1], c = w.ws->cl[2];
+  bool big = false;
+  if (w.lane == 0) {
+    if (a & LONG_CLAUSE) {
+      const int64_t cl = w.c0 + (a & ~LONG_CLAUSE);
+      for (int64_t q = w.S->cb[cl]; q < w.S->cb[cl + 1]; q++) {
+        uint32_t v = code_of(w.S->lits[q]) >> 1;
+        w.act[v] += w.inc;
+        big |= w.act[v] > 1e20f;
+      }
+    } else {
+      uint32_t x[3] = {a, b, c};
+      for (int k = 0; k < 3; k++)
+        if (x[k] != NONE) {
+          uint32_t v = x[k] >> 1;
+          w.act[v] += w.inc;
+          big |= w.act[v] > 1e20f;
+        }
+    }
+  }
+  w.inc *= (1.0f / 0.95f);
+  big = __shfl_sync(FULL, (int)big, 0) || w.inc > 1e20f;
+  __syncwarp();
+  if (big) {
+    for (uint32_t v = w.lane; v < w.V; v += 32) w.act[v] *= 1e-20f;
+    w.inc *= 1e-20f;
+    __syncwarp();
+  }
+}
+
+// Chronological backtrack after a conflict. Returns false when no decision
+// above the assumptions is left to flip (the subtree is refuted).
+__device__ bool backtrack(Warp& w) {
+  uint32_t nd = w.nd;
+  if (w.lane == 0)
+    while (nd > w.nd_fixed && (w.dstack[nd - 1] & FLIP)) nd--;
+  nd = __shfl_sync(FULL, nd, 0);
+  __syncwarp();
+  if (nd <= w.nd_fixed) return false;
+  const uint32_t pos = w.dstack[nd - 1] & ~FLIP;
+  const uint32_t tail = *(volatile uint32_t*)&w.ws->tail;
+  const uint32_t d = w.trail[pos];
+  w.undone += tail - pos;
+  for (uint32_t t = pos + w.lane; t < tail; t += 32) {
+    uint32_t v = w.trail[t] >> 1;
+    atomicAnd(&w.asg[v >> 4], ~(3u << ((v & 15u) * 2u)));
+  }
+  __syncwarp();
+  if (w.lane == 0) {
+    w.dstack[nd - 1] |= FLIP;
+    w.ws->tail = pos;
+    w.ws->conflict = 0;
+  }
+  __syncwarp();
+  w.nd = nd;
+  w.head = pos;
+  if (w.lane == 0) imply(w, d ^ 1u);
+  __syncwarp();
+  return true;
+}
+
+// Highest-activity unassigned variable (ties: lowest id); NONE if all assigned.
+__device__ uint32_t pick(Warp& w) {
+  float best_a = -1.0f;
+  uint32_t best_v = NONE;
+  const uint32_t nwords = (w.V + 15u) >> 4;
+  for (uint32_t k = w.lane; k < nwords; k += 32) {
+    const uint32_t word = w.asg[k];
+    uint32_t un = ~(word | (word >> 1)) & 0x55555555u;  // 00 pairs
+    const uint32_t lim = w.V - 16u * k;
+    if (lim < 16u) un &= (1u << (2u * lim)) - 1u;
+    while (un) {
+      const uint32_t bitpos = __ffs(un) - 1;
+      un &= un - 1u;
+      const uint32_t v = 16u * k + (bitpos >> 1);
+      const float a = w.act[v];
+      if (a > best_a || (a == best_a && v < best_v)) {
+        best_a = a;
+        best_v = v;
+      }
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    float oa = __shfl_xor_sync(FULL, best_a, d);
+    uint32_t ov = __shfl_xor_sync(FULL, best_v, d);
+    if (oa > best_a || (oa == best_a && ov < best_v)) {
+      best_a = oa;
+      best_v = ov;
+    }
+  }
+  return best_v;
+}
+
+__device__ __forceinline__ void set_status(const Solve& S, int32_t st) {
+  atomicCAS(&S.ctrl->status, 0, st);
+}
+
+// ---- job ring (bounded MPMC queue, Vyukov) --------------------------------
+
+__device__ bool ring_push(const Solve& S, const Warp& w, int inst, uint32_t plen,
+                          const uint32_t* prefix_src_trail, const uint32_t* dpos,
+                          uint32_t flip_index) {
+  // called by all lanes; lane 0 reserves
+  Ctrl* C = S.ctrl;
+  uint32_t slot = NONE;
+  if (w.lane == 0) {
+    for (int it = 0; it < 64; it++) {
+      uint32_t pos = *(volatile uint32_t*)&C->q_tail;
+      Job* cell = &S.ring[pos & (S.ring_cap - 1)];
+      uint32_t seq = *(volatile uint32_t*)&cell->seq;
+      int32_t dif = (int32_t)(seq - pos);
+      if (dif == 0) {
+        if (atomicCAS(&C->q_tail, pos, pos + 1) == pos) { slot = pos; break; }
+      } else if (dif < 0) {
+        break;  // full
+      }
+    }
+  }
+  slot = __shfl_sync(FULL, slot, 0);
+  if (slot == NONE) return false;
+  Job* cell = &S.ring[slot & (S.ring_cap - 1)];
+  // prefix = decision literals 0..flip_index-1 as assigned now, then the
+  // negation of decision flip_index
+  for (uint32_t k = w.lane; k < plen; k += 32) {
+    uint32_t lit = prefix_src_trail[dpos[k] & ~FLIP];
+    if (k == flip_index) lit ^= 1u;
+    cell->lit[k] = lit;
+  }
+  if (w.lane == 0) {
+    cell->inst = inst;
+    cell->len = (int32_t)plen;
+  }
+  __threadfence();
+  __syncwarp();
+  if (w.lane == 0) atomicExch(&cell->seq, slot + 1);
+  __syncwarp();
+  return true;
+}
+
+// Try to take a job; returns slot or NONE.
+__device__ uint32_t ring_pop(const Solve& S, int lane) {
+  Ctrl* C = S.ctrl;
+  uint32_t slot = NONE;
+  if (lane == 0) {
+    for (int it = 0; it < 64; it++) {
+      uint32_t pos = *(volatile uint32_t*)&C->q_head;
+      Job* cell = &S.ring[pos & (S.ring_cap - 1)];
+      uint32_t seq = *(volatile uint32_t*)&cell->seq;
+      int32_t dif = (int32_t)(seq - (pos + 1));
+      if (dif == 0) {
+        if (atomicCAS(&C->q_head, pos, pos + 1) == pos) { slot = pos; break; }
+      } else if (dif < 0) {
+        break;  // empty
+      }
+    }
+    __threadfence();  // acquire: the cell's contents after its sequence number
+  }
+  slot = __shfl_sync(FULL, slot, 0);
+  __syncwarp();
+  return slot;
+}
+
+__device__ void ring_release(const Solve& S, uint32_t slot, int lane) {
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence();
+    atomicExch(&S.ring[slot & (S.ring_cap - 1)].seq, slot + S.ring_cap);
+  }
+  __syncwarp();
+}
+
+// An instance's job finished with result r (SCUBA_SAT / SCUBA_UNSAT /
+// SCUBA_UNKNOWN). The last open job of an instance writes its verdict.
+__device__ void finish_job(const Solve& S, Warp& w, int inst, int r) {
+  if (w.lane == 0) {
+    if (r == SCUBA_SAT) {
+      S.verdict[inst] = SCUBA_SAT;
+      atomicOr(&S.done[inst], 1u);
+    } else if (r == SCUBA_UNKNOWN) {
+      atomicOr(&S.done[inst], 2u);  // mark: some subtree gave up
+    }
+    uint32_t left = atomicSub(&S.pending[inst], 1u) - 1u;
+    if (left == 0u) {
+      uint32_t d = atomicOr(&S.done[inst], 4u);
+      if (!(d & 1u)) S.verdict[inst] = (d & 2u) ? SCUBA_UNKNOWN : SCUBA_UNSAT;
+      atomicSub(&S.ctrl->inst_left, 1u);
+    }
+    if (S.stats) {
+      unsigned long long* st = (unsigned long long*)&S.stats[SCUBA_NSTATS * (int64_t)inst];
+      atomicAdd(st + 0, (unsigned long long)w.decisions);
+      atomicAdd(st + 1, (unsigned long long)w.conflicts);
+      atomicAdd(st + 2, (unsigned long long)w.props);
+      atomicAdd(st + 3, (unsigned long long)w.visits);
+      atomicAdd(st + 4, (unsigned long long)w.act_reads);
+      atomicAdd(st + 5, (unsigned long long)w.undone);
+    }
+  }
+  __syncwarp();
+}
+
+// Solve one subtree (inst + assumptions). Returns SAT / UNSAT / UNKNOWN.
+__device__ int run_job(const Solve& S, Warp& w, int inst, const Job* job, int& abort_code) {
+  w.inst = inst;
+  w.V = (uint32_t)S.nv[inst];
+  w.c0 = S.icb[inst];
+  w.occ = S.occ_begin + S.occ_base[inst];
+  const int64_t lbase = S.icb[inst] < S.icb[inst + 1] ? S.cb[S.icb[inst]] : 0;
+  w.ent = S.ent + lbase;
+  w.head = 0;
+  w.nd = 0;
+  w.nd_fixed = 0;
+  w.inc = 1.0f;
+  w.decisions = w.conflicts = w.props = w.visits = w.act_reads = w.undone = 0;
+  const uint32_t nwords = (w.V + 15u) >> 4;
+  for (uint32_t k = w.lane; k < nwords; k += 32) w.asg[k] = 0u;
+  for (uint32_t v = w.lane; v < w.V; v += 32) w.act[v] = 0.0f;
+  if (w.lane == 0) {
+    w.ws->tail = 0;
+    w.ws->conflict = 0;
+  }
+  __syncwarp();
+  if (S.flags[inst] & F_EMPTY) return SCUBA_UNSAT;
+  // level 0: unit clauses, then the job's assumptions as fixed decisions
+  const uint32_t nu = S.nunits[inst];
+  const uint32_t* un = S.units + w.c0;
+  for (uint32_t k = w.lane; k < nu; k += 32)
+    if (!imply(w, un[k])) record_conflict(w, un[k], NONE, NONE);
+  __syncwarp();
+  if (w.ws->conflict) return SCUBA_UNSAT;
+  if (job) {
+    for (int k = 0; k < job->len; k++) {
+      if (bcp(w)) return SCUBA_UNSAT;
+      const uint32_t l = job->lit[k];
+      const uint32_t val = lit_value(w.asg, l);
+      if (val == LV_F) return SCUBA_UNSAT;
+      if (val == LV_T) continue;
+      if (w.lane == 0) {
+        w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail | FLIP;
+        imply(w, l);
+      }
+      w.nd++;
+      __syncwarp();
+    }
+    w.nd_fixed = w.nd;
+  }
+  uint32_t iter = 0;
+  for (;;) {
+    if ((++iter & 63u) == 0u) {
+      int stop = 0;
+      if (w.lane == 0) {
+        if (S.abort_flag && *S.abort_flag) stop = 1;
+        else if (globaltimer() - S.ctrl->t0 > S.time_ns) stop = 2;
+        else if (*(volatile uint32_t*)&S.done[inst] & 1u) stop = 3;  // solved elsewhere
+      }
+      stop = __shfl_sync(FULL, stop, 0);
+      if (stop == 1) { abort_code = SCUBA_ERR_ABORTED; return SCUBA_UNKNOWN; }
+      if (stop == 2) { abort_code = SCUBA_ERR_TIMEOUT; return SCUBA_UNKNOWN; }
+      if (stop == 3) return SCUBA_UNSAT;  // the instance is SAT already; this subtree is moot
+    }
+    if (bcp(w)) {
+      w.conflicts++;
+      bump(w);
+      if (!backtrack(w)) return SCUBA_UNSAT;
+      continue;
+    }
+    w.act_reads += w.V - *(volatile uint32_t*)&w.ws->tail;
+    const uint32_t v = pick(w);
+    if (v == NONE) {
+      // the first subtree of the instance to reach a model writes it
+      uint32_t won = 0;
+      if (w.lane == 0) won = !(atomicOr(&S.done[inst], 8u) & 8u);
+      won = __shfl_sync(FULL, won, 0);
+      if (won && S.model)
+        for (uint32_t x = w.lane; x < w.V; x += 32) {
+          uint32_t bits = (w.asg[x >> 4] >> ((x & 15u) * 2u)) & 3u;
+          S.model[S.vb[inst] + x] = bits == 1u ? 1 : 0;
+        }
+      __syncwarp();
+      return SCUBA_SAT;
+    }
+    // budget: decisions of the instance across all of its subtrees
+    if (S.budget > 0 && (w.decisions & 255) == 0) {
+      unsigned long long tot = 0;
+      if (w.lane == 0) tot = atomicAdd(&S.inst_dec[inst], 256ull);
+      tot = __shfl_sync(FULL, tot, 0);
+      if ((int64_t)tot >= S.budget) return SCUBA_UNKNOWN;
+    }
+    // share the untried branch of the shallowest open decision
+    if (S.split && (w.decisions % S.split_interval) == 0 && w.nd > w.nd_fixed) {
+      uint32_t idle = 0;
+      if (w.lane == 0) idle = *(volatile uint32_t*)&S.ctrl->idle;
+      idle = __shfl_sync(FULL, idle, 0);
+      if (idle > 0) {
+        uint32_t k = w.nd_fixed;
+        if (w.lane == 0)
+          while (k < w.nd && (w.dstack[k] & FLIP)) k++;
+        k = __shfl_sync(FULL, k, 0);
+        if (k < w.nd && k + 1 <= (uint32_t)MAX_PREFIX) {
+          if (w.lane == 0) atomicAdd(&S.pending[inst], 1u);
+          __syncwarp();
+          if (ring_push(S, w, inst, k + 1, w.trail, w.dstack, k)) {
+            if (w.lane == 0) {
+              w.dstack[k] |= FLIP;
+              atomicAdd(&S.ctrl->jobs_split, 1u);
+            }
+          } else if (w.lane == 0) {
+            atomicSub(&S.pending[inst], 1u);
+          }
+          __syncwarp();
+        }
+      }
+    }
+    w.decisions++;
+    if (w.lane == 0) {
+      w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
+      imply(w, 2u * v + 1u);  // false first
+    }
+    w.nd++;
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_solve(Solve S) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
+  WarpShared* wsh = reinterpret_cast<WarpShared*>(smem);
+  Warp w;
+  w.S = &S;
+  w.ws = &wsh[wib];
+  w.asg = smem + (sizeof(WarpShared) / 4) * wpb + (size_t)S.assign_words * wib;
+  w.trail = S.trail + slot * S.vmax;
+  w.dstack = S.dstack + slot * S.vmax;
+  w.act = S.act + slot * S.vmax;
+  w.lane = lane;
+  if (batch_failed(S.ctrl)) return;
+  bool counted_idle = false;
+  for (;;) {
+    // 1) a shared subtree, 2) a fresh instance, 3) wait for shared work
+    int inst = -1;
+    uint32_t slot_j = ring_pop(S, lane);
+    const Job* job = nullptr;
+    if (slot_j != NONE) {
+      job = &S.ring[slot_j & (S.ring_cap - 1)];
+      inst = job->inst;
+    } else {
+      uint32_t k = 0;
+      if (lane == 0) k = atomicAdd(&S.ctrl->next_inst, 1u);
+      k = __shfl_sync(FULL, k, 0);
+      if (k < (uint32_t)S.n) {
+        inst = S.order ? S.order[k] : (int)k;
+      } else {
+        if (!counted_idle) {
+          if (lane == 0) atomicAdd(&S.ctrl->idle, 1u);
+          counted_idle = true;
+        }
+        int stop = 0;
+        if (lane == 0) {
+          if (*(volatile uint32_t*)&S.ctrl->inst_left == 0u) stop = 1;
+          else if (*(volatile int32_t*)&S.ctrl->status != 0) stop = 1;
+          else if (S.abort_flag && *S.abort_flag) { stop = 1; set_status(S, SCUBA_ERR_ABORTED); }
+          else if (globaltimer() - S.ctrl->t0 > S.time_ns) { stop = 1; set_status(S, SCUBA_ERR_TIMEOUT); }
+          else __nanosleep(2000);
+        }
+        stop = __shfl_sync(FULL, stop, 0);
+        if (stop) break;
+        continue;
+      }
+    }
+    if (counted_idle) {
+      if (lane == 0) atomicSub(&S.ctrl->idle, 1u);
+      counted_idle = false;
+    }
+    int abort_code = 0;
+    int r;
+    w.decisions = w.conflicts = w.props = w.visits = w.act_reads = w.undone = 0;
+    uint32_t moot = 0;
+    if (lane == 0) moot = *(volatile uint32_t*)&S.done[inst] & 1u;
+    moot = __shfl_sync(FULL, moot, 0);
+    if (S.flags[inst] & F_BAD) {
+      r = SCUBA_UNKNOWN;
+      if (lane == 0) set_status(S, SCUBA_ERR_MALFORMED);
+    } else if (S.nv[inst] > S.vmax) {
+      r = SCUBA_UNKNOWN;
+      if (lane == 0) set_status(S, SCUBA_ERR_TOO_LARGE);
+    } else if (moot) {
+      r = SCUBA_UNSAT;  // moot: another subtree already found a model
+    } else {
+      r = run_job(S, w, inst, job, abort_code);
+    }
+    if (job) ring_release(S, slot_j, lane);
+    finish_job(S, w, inst, r);
+    if (abort_code) {
+      if (lane == 0) set_status(S, abort_code);
+      break;
+    }
+  }
+  if (counted_idle && lane == 0) atomicSub(&S.ctrl->idle, 1u);
+}
+
+// Instances still open when the kernel stopped (timeout / abort) -> UNKNOWN.
+__global__ void k_finalize(Solve S) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+    uint32_t d = S.done[i];
+    if (!(d & 5u)) S.verdict[i] = SCUBA_UNKNOWN;
+  }
+}
+
+__global__ void k_init_ring(Job* ring, uint32_t cap) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x)
+    ring[i].seq = i;
+}
+
+__global__ void k_init_inst(uint32_t* pending, uint32_t* done, unsigned long long* dec, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    pending[i] = 1u;
+    done[i] = 0u;
+    dec[i] = 0ull;
+  }
+}
+
+__global__ void k_start_clock(Ctrl* c) { c->t0 = globaltimer(); }
+
+__global__ void k_init_ctrl(Ctrl* c, uint32_t n) {
+  c->next_inst = 0;
+  c->inst_left = n;
+  c->idle = 0;
+  c->status = 0;
+  c->q_head = 0;
+  c->q_tail = 0;
+  c->t0 = globaltimer();
+  c->jobs_split = 0;
+}
+
+}  // namespace dev
+
+// --------------------------------------------------------------------------
+// Host side: scratch, launch
+// --------------------------------------------------------------------------
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct Scratch {
+  Buf occ_base, norm, occ_cnt, occ_begin, ent, units, nunits, flags;
+  Buf pending, done, inst_dec, trail, dstack, act, ring, ctrl;
+  Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
+  int sms = 0;
+  int32_t last_status = 0;
+};
+
+std::map<int, Scratch>& scratch_map() {
+  static std::map<int, Scratch> m;
+  return m;
+}
+
+int ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return 0;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t want = bytes + bytes / 4;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    want = bytes;
+  }
+  b.cap = want;
+  return 0;
+}
+
+template <class T>
+T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+int cuda_fail(const char* what, cudaError_t e) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return SCUBA_ERR_CUDA;
+}
+
+}  // namespace
+
+}  // namespace scuba
+
+using namespace scuba;
+
+extern "C" int scuba_options_init(scuba_options* o) {
+  if (!o) return SCUBA_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->heuristic = SCUBA_HEUR_ACTIVITY;
+  o->learned_depth = 0;
+  o->decision_budget = 0;
+  o->time_budget_ms = 0;
+  o->split = 1;
+  o->split_interval = 0;
+  return SCUBA_OK;
+}
+
+static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model,
+                      cudaStream_t st, const scuba_options* opt) {
+  if (!b || b->num_instances < 0 || b->total_clauses < 0 || b->total_lits < 0 ||
+      b->max_vars < 0 || b->total_vars < 0) {
+    set_error("scuba_solve_batch: bad arguments");
+    return SCUBA_ERR_ARG;
+  }
+  scuba_options defaults;
+  scuba_options_init(&defaults);
+  if (!opt) opt = &defaults;
+  const int n = b->num_instances;
+  if (n == 0) return SCUBA_OK;
+  if (!verdict) {
+    set_error("scuba_solve_batch: NULL verdict array");
+    return SCUBA_ERR_ARG;
+  }
+  if (!b->inst_clause_begin || !b->clause_begin || !b->inst_num_vars || !b->inst_var_begin ||
+      (b->total_lits > 0 && !b->lits)) {
+    set_error("scuba_solve_batch: NULL batch array");
+    return SCUBA_ERR_ARG;
+  }
+  if (opt->heuristic != SCUBA_HEUR_ACTIVITY && opt->heuristic != SCUBA_HEUR_LEARNED) {
+    set_error("scuba_solve_batch: unknown heuristic");
+    return SCUBA_ERR_ARG;
+  }
+  if (b->max_vars >= (1 << 29) || b->total_lits >= (1LL << 32)) {
+    set_error("scuba_solve_batch: instance too large");
+    return SCUBA_ERR_TOO_LARGE;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+  Scratch& S = scratch_map()[dev];
+  if (!S.sms) {
+    e = cudaDeviceGetAttribute(&S.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceGetAttribute", e);
+  }
+  const int64_t C = b->total_clauses, L = b->total_lits;
+  const int vmax = std::max(1, (int)b->max_vars);
+  // occurrence offsets: sum over instances of (2V+1)
+  const int64_t occ_total = 2LL * b->total_vars + n;
+
+  // shape: warps per block x blocks per SM (shared memory bounds the warps)
+  int wpb = opt->warps_per_block > 0 ? opt->warps_per_block : 8;
+  int bps = opt->blocks_per_sm > 0 ? opt->blocks_per_sm : 4;
+  wpb = std::min(wpb, 8);
+  const uint32_t assign_words = (uint32_t)((vmax + 15) / 16);
+  size_t smem = (sizeof(dev::WarpShared) + (size_t)assign_words * 4) * wpb;
+  const size_t smem_cap = 227 * 1024;
+  while (wpb > 1 && smem > smem_cap) {
+    wpb--;
+    smem = (sizeof(dev::WarpShared) + (size_t)assign_words * 4) * wpb;
+  }
+  if (smem > smem_cap) {
+    set_error("scuba_solve_batch: instance too large for shared-memory assignment");
+    return SCUBA_ERR_TOO_LARGE;
+  }
+  while (bps > 1 && smem * bps > 228 * 1024) bps--;
+  const int64_t slots = (int64_t)S.sms * bps * wpb;
+  const uint32_t ring_cap = 4096;
+
+  if (ensure(S.occ_base, 8 * (size_t)(n + 1)) || ensure(S.norm, 4 * (size_t)L) ||
+      ensure(S.occ_cnt, 4 * (size_t)occ_total) || ensure(S.occ_begin, 4 * (size_t)occ_total) ||
+      ensure(S.ent, 8 * (size_t)L) || ensure(S.units, 4 * (size_t)std::max<int64_t>(C, 1)) ||
+      ensure(S.nunits, 4 * (size_t)n) || ensure(S.flags, 4 * (size_t)n) ||
+      ensure(S.pending, 4 * (size_t)n) || ensure(S.done, 4 * (size_t)n) ||
+      ensure(S.inst_dec, 8 * (size_t)n) || ensure(S.trail, 4 * (size_t)slots * vmax) ||
+      ensure(S.dstack, 4 * (size_t)slots * vmax) || ensure(S.act, 4 * (size_t)slots * vmax) ||
+      ensure(S.ring, sizeof(dev::Job) * (size_t)ring_cap) || ensure(S.ctrl, sizeof(dev::Ctrl))) {
+    set_error("scuba_solve_batch: out of device memory for scratch");
+    return SCUBA_ERR_NOMEM;
+  }
+  dev::Prep pr;
+  pr.n = n;
+  pr.C = C;
+  pr.L = L;
+  pr.icb = b->inst_clause_begin;
+  pr.cb = b->clause_begin;
+  pr.lits = b->lits;
+  pr.nv = b->inst_num_vars;
+  pr.occ_base = P<int64_t>(S.occ_base);
+  pr.norm = P<uint32_t>(S.norm);
+  pr.occ_cnt = P<uint32_t>(S.occ_cnt);
+  pr.occ_begin = P<uint32_t>(S.occ_begin);
+  pr.ent = P<uint64_t>(S.ent);
+  pr.units = P<uint32_t>(S.units);
+  pr.nunits = P<uint32_t>(S.nunits);
+  pr.flags = P<uint32_t>(S.flags);
+  pr.total_vars = b->total_vars;
+  pr.occ_cap = occ_total;
+  pr.vmax = vmax;
+  pr.vb = b->inst_var_begin;
+  pr.ctrl = P<dev::Ctrl>(S.ctrl);
+
+  dev::k_init_ctrl<<<1, 1, 0, st>>>(pr.ctrl, (uint32_t)n);
+  cudaMemsetAsync(pr.occ_cnt, 0, 4 * (size_t)occ_total, st);
+  cudaMemsetAsync(pr.flags, 0, 4 * (size_t)n, st);
+  dev::k_occ_base<<<1, 1024, 0, st>>>(pr);
+  if (C > 0) {
+    int grid = (int)std::min<int64_t>((C + 255) / 256, (int64_t)S.sms * 32);
+    dev::k_normalize<<<grid, 256, 0, st>>>(pr);
+  }
+  int wgrid = (int)std::min<int64_t>((n + 7) / 8, (int64_t)S.sms * 16);
+  dev::k_occ_scan<<<wgrid, 256, 0, st>>>(pr);
+  dev::k_fill<<<wgrid, 256, 0, st>>>(pr);
+
+  dev::Solve sv;
+  sv.n = n;
+  sv.vmax = vmax;
+  sv.assign_words = assign_words;
+  sv.icb = b->inst_clause_begin;
+  sv.cb = b->clause_begin;
+  sv.lits = b->lits;
+  sv.nv = b->inst_num_vars;
+  sv.vb = b->inst_var_begin;
+  sv.occ_base = pr.occ_base;
+  sv.occ_begin = pr.occ_begin;
+  sv.ent = pr.ent;
+  sv.units = pr.units;
+  sv.nunits = pr.nunits;
+  sv.flags = pr.flags;
+  sv.order = opt->order;
+  sv.verdict = verdict;
+  sv.model = model;
+  sv.stats = opt->stats;
+  sv.pending = P<uint32_t>(S.pending);
+  sv.done = P<uint32_t>(S.done);
+  sv.inst_dec = P<unsigned long long>(S.inst_dec);
+  sv.trail = P<uint32_t>(S.trail);
+  sv.dstack = P<uint32_t>(S.dstack);
+  sv.act = P<float>(S.act);
+  sv.ring = P<dev::Job>(S.ring);
+  sv.ring_cap = ring_cap;
+  sv.ctrl = P<dev::Ctrl>(S.ctrl);
+  sv.budget = opt->decision_budget;
+  int64_t tb = opt->time_budget_ms > 0 ? opt->time_budget_ms : 600000;
+  sv.time_ns = (uint64_t)tb * 1000000ull;
+  sv.abort_flag = opt->abort_flag;
+  sv.split = opt->split ? 1 : 0;
+  sv.split_interval = opt->split_interval > 0 ? opt->split_interval : 16;
+
+  dev::k_init_ring<<<16, 256, 0, st>>>(sv.ring, ring_cap);
+  dev::k_init_inst<<<(n + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec, n);
+  dev::k_start_clock<<<1, 1, 0, st>>>(sv.ctrl);
+  e = cudaFuncSetAttribute(dev::k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
+  if (opt->search_event_begin) cudaEventRecord((cudaEvent_t)opt->search_event_begin, st);
+  dev::k_solve<<<S.sms * bps, 32 * wpb, smem, st>>>(sv);
+  if (opt->search_event_end) cudaEventRecord((cudaEvent_t)opt->search_event_end, st);
+  dev::k_finalize<<<(n + 255) / 256, 256, 0, st>>>(sv);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("kernel launch", e);
+  return SCUBA_OK;
+}
+
+extern "C" int scuba_solve_batch_ex(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model,
+                                    void* stream, const scuba_options* opt) {
+  return solve_impl(b, verdict, model, (cudaStream_t)stream, opt);
+}
+
+extern "C" int scuba_solve_batch(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model,
+                                 void* stream) {
+  return solve_impl(b, verdict, model, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int scuba_sync_status(void* stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail("cudaStreamSynchronize", e);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto it = scratch_map().find(dev);
+  if (it == scratch_map().end() || !it->second.ctrl.p) return SCUBA_OK;
+  dev::Ctrl c;
+  e = cudaMemcpy(&c, it->second.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("cudaMemcpy", e);
+  if (c.status != 0) set_error("device status " + std::to_string(c.status));
+  return c.status;
+}
+
+extern "C" int scuba_solve_batch_host(const scuba_cnf_batch* hb, uint8_t* verdict,
+                                      uint8_t* model, void* stream, const scuba_options* opt) {
+  if (!hb || !verdict || hb->num_instances < 0) return SCUBA_ERR_ARG;
+  const int n = hb->num_instances;
+  if (n == 0) return SCUBA_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  Scratch& S = scratch_map()[dev];
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t C = hb->total_clauses, L = hb->total_lits;
+  const int64_t nvars = hb->inst_var_begin[n];
+  if (ensure(S.h_icb, 8 * (size_t)(n + 1)) || ensure(S.h_cb, 8 * (size_t)(C + 1)) ||
+      ensure(S.h_lits, 4 * (size_t)L) || ensure(S.h_nv, 4 * (size_t)n) ||
+      ensure(S.h_vb, 8 * (size_t)(n + 1)) || ensure(S.h_verdict, (size_t)n) ||
+      ensure(S.h_model, (size_t)std::max<int64_t>(nvars, 1)) ||
+      ensure(S.h_stats, 8 * SCUBA_NSTATS * (size_t)n))
+    return SCUBA_ERR_NOMEM;
+  cudaError_t e;
+  e = cudaMemcpyAsync(S.h_icb.p, hb->inst_clause_begin, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S.h_cb.p, hb->clause_begin, 8 * (size_t)(C + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && L > 0) e = cudaMemcpyAsync(S.h_lits.p, hb->lits, 4 * (size_t)L, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S.h_nv.p, hb->inst_num_vars, 4 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S.h_vb.p, hb->inst_var_begin, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync H2D", e);
+  scuba_cnf_batch db = *hb;
+  db.inst_clause_begin = P<int64_t>(S.h_icb);
+  db.clause_begin = P<int64_t>(S.h_cb);
+  db.lits = P<int32_t>(S.h_lits);
+  db.inst_num_vars = P<int32_t>(S.h_nv);
+  db.inst_var_begin = P<int64_t>(S.h_vb);
+  scuba_options o;
+  if (opt) o = *opt; else scuba_options_init(&o);
+  int64_t* host_stats = o.stats;
+  if (host_stats) {
+    cudaMemsetAsync(S.h_stats.p, 0, 8 * SCUBA_NSTATS * (size_t)n, st);
+    o.stats = P<int64_t>(S.h_stats);
+  }
+  int r = solve_impl(&db, P<uint8_t>(S.h_verdict), model ? P<uint8_t>(S.h_model) : nullptr, st, &o);
+  if (r != SCUBA_OK) return r;
+  e = cudaMemcpyAsync(verdict, S.h_verdict.p, (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && model && nvars > 0)
+    e = cudaMemcpyAsync(model, S.h_model.p, (size_t)nvars, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && host_stats)
+    e = cudaMemcpyAsync(host_stats, S.h_stats.p, 8 * SCUBA_NSTATS * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync D2H", e);
+  return scuba_sync_status(stream);
+}
+
+extern "C" void scuba_release(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  auto it = scratch_map().find(dev);
+  if (it == scratch_map().end()) return;
+  Scratch& S = it->second;
+  Buf* all[] = {&S.occ_base, &S.norm, &S.occ_cnt, &S.occ_begin, &S.ent, &S.units, &S.nunits,
+                &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
+                &S.ring, &S.ctrl, &S.h_icb, &S.h_cb, &S.h_lits, &S.h_nv, &S.h_vb,
+                &S.h_verdict, &S.h_model, &S.h_stats};
+  for (Buf* x : all) {
+    if (x->p) cudaFree(x->p);
+    x->p = nullptr;
+    x->cap = 0;
+  }
+  scratch_map().erase(it);
+}

@@ -1,0 +1,193 @@
+"""GPU parity: verdicts of the CUDA DPLL (through the C ABI) against the CPU
+oracle on the same seeded inputs, bit-exact; every SAT model re-verified on
+the host against the original integer constraints (or the clauses)."""
+import glob
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from closed_forms import partition_algebra
+from ir_eval import cnf_satisfied
+from workloads import queries
+from workloads.ir import parse_text
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_21552_gb300 import build
+    build.build()
+    from paper_2601_21552_gb300 import api as A
+    return A
+
+
+def _check_queries(api, irs, **opts):
+    res = api.solve_queries(irs, time_budget_ms=120000, **opts)
+    assert res["status"] == 0
+    assert res["fails"] == 0, "a SAT model violates the original constraints"
+    assert ((res["verdict"] == 1) == (res["verified"] == 1)).all()
+    return res
+
+
+def test_config1_full(api):
+    irs, _ = queries.config1(256)
+    res = _check_queries(api, irs)
+    ref = oracle.solve_queries(irs)["verdict"]
+    assert (res["verdict"] == ref).all()
+    assert set(ref.tolist()) == {0, 1}
+
+
+@pytest.mark.parametrize("split", [True, False])
+def test_config2_w10_vs_oracle(api, split):
+    irs, _ = queries.config2(512, w=10)
+    res = _check_queries(api, irs, split=split)
+    ref = oracle.solve_queries(irs)["verdict"]
+    assert (res["verdict"] == ref).all()
+
+
+def test_config2_full_size(api):
+    """4,096 partition queries at 16 bits, in the benchmark's launch shape,
+    against the stored oracle verdicts (pinned by the closed form)."""
+    stored = np.array([int(x) for x in open(os.path.join(
+        GOLDEN, "config2_w16_oracle_verdicts.txt")).read().split()], np.uint8)
+    irs, params = queries.config2(4096)
+    res = _check_queries(api, irs)
+    assert (res["verdict"] == stored).all()
+    # spot-check a few against the closed form directly
+    for i in range(0, 4096, 257):
+        assert res["verdict"][i] == (1 if partition_algebra(**params[i]) else 0)
+
+
+def test_worked_examples(api):
+    files = sorted(glob.glob(os.path.join(GOLDEN, "*.sq")))
+    parsed = [parse_text(open(f).read()) for f in files]
+    irs = [p[0].to_array() for p in parsed]
+    res = _check_queries(api, irs)
+    want = np.array([1 if p[1]["expect"] == "SAT" else 0 for p in parsed], np.uint8)
+    assert (res["verdict"] == want).all(), [os.path.basename(f) for f, a, b in
+                                            zip(files, res["verdict"], want) if a != b]
+
+
+# ---------------------------------------------------------------------------
+# Raw CNF batches (random 3-SAT, long clauses, degenerate cases)
+# ---------------------------------------------------------------------------
+
+def _pack(cnfs):
+    """[(nvars, list of clauses)] -> host CSR arrays."""
+    icb, cb, lits, nv, vb = [0], [0], [], [], [0]
+    for n, cls in cnfs:
+        for c in cls:
+            lits.extend(c)
+            cb.append(len(lits))
+        icb.append(len(cb) - 1)
+        nv.append(n)
+        vb.append(vb[-1] + n)
+    return (np.array(icb, np.int64), np.array(cb, np.int64), np.array(lits or [0], np.int32),
+            np.array(nv or [0], np.int32), np.array(vb, np.int64), len(lits))
+
+
+def _solve_raw(api, cnfs, **opts):
+    from paper_2601_21552_gb300 import binding as B
+    icb, cb, lits, nv, vb, L = _pack(cnfs)
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(a).to(dev)
+    d_icb, d_cb, d_lits, d_nv, d_vb = t(icb), t(cb), t(lits), t(nv), t(vb)
+    n = len(cnfs)
+    b = B.make_batch(n, int(max(nv.max(), 0)) if n else 0, len(cb) - 1, L, int(vb[-1]),
+                     d_icb.data_ptr(), d_cb.data_ptr(), d_lits.data_ptr(), d_nv.data_ptr(),
+                     d_vb.data_ptr())
+    verdict = torch.full((max(n, 1),), 9, dtype=torch.uint8, device=dev)
+    model = torch.zeros(max(int(vb[-1]), 1), dtype=torch.uint8, device=dev)
+    stats = torch.zeros((max(n, 1), B.SCUBA_NSTATS), dtype=torch.int64, device=dev)
+    o = api.options(stats=stats, time_budget_ms=opts.pop("time_budget_ms", 60000), **opts)
+    B.scuba_solve_batch_ex(b, verdict.data_ptr(), model.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream, o)
+    st = B.scuba_sync_status(torch.cuda.current_stream().cuda_stream)
+    return st, verdict.cpu().numpy()[:n], model.cpu().numpy(), vb, stats.cpu().numpy()[:n]
+
+
+def _model_ok(cls, model, base):
+    return all(any((model[base + abs(l) - 1] == 1) == (l > 0) for l in c) for c in cls)
+
+
+def test_random_3sat_vs_oracle(api):
+    cnfs = []
+    for s in range(300):
+        n, l = queries.random_3sat(70000 + s, 40, 90)
+        cnfs.append((n, l.tolist()))
+    st, v, m, vb, stats = _solve_raw(api, cnfs)
+    assert st == 0
+    ocnfs = [oracle.CNF(n, np.arange(0, 3 * len(c) + 1, 3), np.array(c, np.int32).reshape(-1))
+             for n, c in cnfs]
+    ref = oracle.solve_cnfs(ocnfs)["verdict"]
+    assert (v == ref).all()
+    for i, (n, c) in enumerate(cnfs):
+        if v[i] == 1:
+            assert _model_ok(c, m, vb[i])
+    assert (stats[:, 2] > 0).all()
+
+
+def test_long_clauses_and_duplicates(api):
+    rng = np.random.default_rng(3)
+    cnfs = []
+    for s in range(200):
+        n = int(rng.integers(8, 24))
+        cls = []
+        for _ in range(int(rng.integers(n, 4 * n))):
+            k = int(rng.integers(1, 8))
+            c = [int(rng.integers(1, n + 1)) * (1 if rng.random() < 0.5 else -1) for _ in range(k)]
+            cls.append(c)
+        cnfs.append((n, cls))
+    st, v, m, vb, _ = _solve_raw(api, cnfs)
+    assert st == 0
+    for i, (n, cls) in enumerate(cnfs):
+        cnf = oracle.CNF(n, np.cumsum([0] + [len(c) for c in cls]),
+                         np.array([x for c in cls for x in c] or [1], np.int32)[:sum(len(c) for c in cls)])
+        want = oracle.dpll(cnf)["verdict"]
+        assert v[i] == want, i
+        if v[i] == 1:
+            assert _model_ok(cls, m, vb[i])
+
+
+def test_degenerate_instances(api):
+    cnfs = [
+        (3, []),                         # no clauses: SAT
+        (2, [[1, 2], []]),               # empty clause: UNSAT
+        (1, [[1], [-1]]),                # contradicting units: UNSAT
+        (2, [[1, 1, 2], [-2]]),          # duplicate literal: SAT with x1
+        (2, [[1, -1], [2, -2, 1]]),      # tautologies only: SAT
+        (0, []),                         # zero variables
+        (4, [[1, 2, 3, 4], [-1], [-2], [-3]]),  # long clause made unit: x4
+    ]
+    st, v, m, vb, _ = _solve_raw(api, cnfs)
+    assert st == 0
+    assert v.tolist() == [1, 0, 0, 1, 1, 1, 1]
+    assert m[vb[3]] == 1 and m[vb[6] + 3] == 1
+
+
+def test_malformed_literal_reported(api):
+    cnfs = [(2, [[1, 3]]), (2, [[1, 2]])]
+    st, v, m, vb, _ = _solve_raw(api, cnfs)
+    assert st == -5  # SCUBA_ERR_MALFORMED
+    assert v[0] == 2
+
+
+def test_decision_budget_gives_unknown(api):
+    n, l = queries.random_3sat(4242, 150, 150)
+    st, v, m, vb, stats = _solve_raw(api, [(n, l.tolist())], decision_budget=300, split=False)
+    assert st == 0 and v[0] == 2
+
+
+def test_empty_batch(api):
+    from paper_2601_21552_gb300 import binding as B
+    b = B.make_batch(0, 0, 0, 0, 0, None, None, None, None, None)
+    assert B.scuba_solve_batch(b, None, None, None) == 0

@@ -1,0 +1,180 @@
+"""Host-side product code on the CPU: the C ABI library loads and exports
+every symbol of include/scuba.h, the 3-CNF encoder is equisatisfiable with the
+integer semantics input by input, and the host re-verifier agrees with an
+independent big-integer evaluator. No GPU calls."""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+from ir_eval import evaluate
+from workloads import queries
+from workloads.ir import IR, parse_text
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2601_21552_gb300 import build
+    build.build()
+    from paper_2601_21552_gb300 import binding
+    return binding
+
+
+def test_exports_every_header_symbol(B):
+    hdr = open(os.path.join(ROOT, "include", "scuba.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(scuba_[a-z_]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    for name in sorted(names):
+        assert hasattr(B._lib, name), name
+    assert set(B.EXPORTED) == names
+
+
+def _unit_propagate(nv, clauses, assign):
+    """Plain unit propagation; returns False on conflict."""
+    changed = True
+    while changed:
+        changed = False
+        for cl in clauses:
+            open_l, sat = [], False
+            for l in cl:
+                v = assign.get(abs(l))
+                if v is None:
+                    if l not in open_l:
+                        open_l.append(l)
+                elif v == (l > 0):
+                    sat = True
+                    break
+            if sat:
+                continue
+            if not open_l:
+                return False
+            if len(open_l) == 1:
+                assign[abs(open_l[0])] = open_l[0] > 0
+                changed = True
+    return True
+
+
+def _cnf_sat_under(nv, clauses, fixed):
+    """Is the CNF satisfiable with the given variables fixed? Unit propagation,
+    then brute force over what is left (tiny gadgets only)."""
+    assign = dict(fixed)
+    if not _unit_propagate(nv, clauses, assign):
+        return False
+    rest = [v for v in range(1, nv + 1) if v not in assign]
+    assert len(rest) <= 14, "gadget too large for the exhaustive check"
+    for bits in itertools.product([False, True], repeat=len(rest)):
+        a = dict(assign)
+        a.update(zip(rest, bits))
+        if all(any(a[abs(l)] == (l > 0) for l in cl) for cl in clauses):
+            return True
+    return False
+
+
+def _gadgets():
+    out = []
+    for op in ("add", "mul", "div3", "rem5", "div4", "ult", "ule", "eq", "orcmp"):
+        for t in range(0, 20, 3):
+            ir = IR()
+            x = ir.free(3)
+            y = ir.free(3)
+            if op == "add":
+                ir.assert_(ir.eq(ir.add(x, y), ir.const(t)))
+            elif op == "mul":
+                ir.assert_(ir.ult(ir.mul(x, y), ir.const(t)))
+            elif op == "div3":
+                ir.assert_(ir.eq(ir.udiv(ir.add(x, y), 3), ir.const(t % 5)))
+            elif op == "rem5":
+                ir.assert_(ir.eq(ir.urem(ir.mul(x, y), 5), ir.const(t % 5)))
+            elif op == "div4":
+                ir.assert_(ir.ule(ir.udiv(ir.mul(x, y), 4), ir.const(t % 13)))
+            elif op == "ult":
+                ir.assert_(ir.ult(ir.add(x, ir.const(t % 7)), y))
+            elif op == "ule":
+                ir.assert_(ir.not_(ir.ule(ir.mul(x, ir.const(t % 5 + 1)), y)))
+            elif op == "eq":
+                ir.assert_(ir.or_(ir.eq(x, ir.const(t % 8)), ir.eq(ir.add(x, y), ir.const(t))))
+            else:
+                ir.assert_(ir.or_(ir.ult(x, y), ir.and_(ir.ule(y, x), ir.eq(y, ir.const(t % 8)))))
+            out.append((op, t, ir))
+    return out
+
+
+@pytest.mark.parametrize("case", _gadgets(), ids=lambda c: f"{c[0]}-{c[1]}")
+def test_encoder_equisatisfiable_per_input(B, case):
+    op, t, ir = case
+    a = ir.to_array()
+    enc = B.scuba_encode_batch([a])
+    cb, lits = enc.clause_begin, enc.lits
+    clauses = [lits[cb[i]:cb[i + 1]].tolist() for i in range(enc.total_clauses)]
+    assert all(len(c) <= 3 for c in clauses), "encoder must emit 3-CNF"
+    iib, widths, var = enc.inputs()
+    assert widths.tolist() == [3, 3]
+    for xv in range(8):
+        for yv in range(8):
+            fixed = {}
+            for k in range(3):
+                fixed[int(var[k])] = bool((xv >> k) & 1)
+                fixed[int(var[3 + k])] = bool((yv >> k) & 1)
+            assert _cnf_sat_under(enc.total_vars, clauses, fixed) == evaluate(a, [xv, yv]), (xv, yv)
+
+
+def test_input_bits_numbered_first_msb_first(B):
+    ir = queries.bounds_query(8, 2, 3, 1, 2, True)
+    enc = B.scuba_encode_batch([ir.to_array()])
+    iib, widths, var = enc.inputs()
+    assert widths.tolist() == [8, 8, 8, 8]
+    # word 0 occupies variables 1..8 with its MSB = 1
+    assert var[:8].tolist() == [8, 7, 6, 5, 4, 3, 2, 1]
+    assert sorted(var.tolist()) == list(range(1, 33))
+
+
+def test_verify_batch_against_big_int_evaluator(B):
+    rng = np.random.default_rng(5)
+    irs = []
+    for i in range(40):
+        p = queries.config1_params(1000 + i, w=6)
+        irs.append(queries.bounds_query(**p).to_array())
+    enc = B.scuba_encode_batch(irs)
+    iib, widths, var = enc.inputs()
+    for trial in range(3):
+        model = rng.integers(0, 2, size=enc.total_vars, dtype=np.uint8)
+        verdict = np.ones(enc.n, np.uint8)
+        fails, ok = B.scuba_verify_batch(enc, verdict, model)
+        vb = enc.inst_var_begin
+        woff = np.concatenate([[0], np.cumsum(widths)])
+        for i in range(enc.n):
+            words = []
+            for k in range(iib[i], iib[i + 1]):
+                w = 0
+                for j in range(widths[k]):
+                    v = int(var[woff[k] + j])
+                    w |= int(model[vb[i] + v - 1]) << j
+                words.append(w)
+            assert ok[i] == (1 if evaluate(irs[i], words) else 0)
+        assert fails == int((ok == 0).sum())
+
+
+def test_encoder_rejects_malformed_ir(B):
+    a = queries.bounds_query(8, 1, 0, 1, 0, True).to_array()
+    bad = a.copy()
+    bad[0] = 7
+    with pytest.raises(RuntimeError):
+        B.scuba_encode_batch([bad])
+    bad = a.copy()
+    bad[4 + 4 * 5 + 1] = 99  # operand pointing forward
+    with pytest.raises(RuntimeError):
+        B.scuba_encode_batch([bad])
+
+
+def test_worked_examples_encode_to_3cnf(B):
+    import glob
+    files = sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "*.sq")))
+    irs = [parse_text(open(f).read())[0].to_array() for f in files]
+    enc = B.scuba_encode_batch(irs)
+    lens = np.diff(enc.clause_begin)
+    assert lens.max() <= 3 and enc.n == len(files)
