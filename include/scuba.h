@@ -92,7 +92,16 @@ typedef struct scuba_options {
   int32_t split;             /* 1: hand DPLL subtrees of busy instances to idle warps */
   int32_t warps_per_block;   /* 0: autotuned default */
   int32_t blocks_per_sm;     /* 0: autotuned default */
-  int32_t split_interval;    /* decisions between checks for idle warps; 0: default */
+  int32_t split_interval;    /* decisions between checks for idle warps; 0: default 16 */
+  int32_t split_min;         /* decisions a subtree makes before it may share work;
+                                0: default 256 */
+  int32_t trail_placement;   /* 0: auto (global), 1: shared memory, 2: global memory */
+  int64_t* finish_ns;        /* profiling, device [num_instances] or NULL: time from
+                                the start of the search to each verdict, in ns */
+  int64_t* profile;          /* profiling, device [8] or NULL, added to: subtrees
+                                shared, subtrees run, prefix literals shared, open
+                                depth left at each share, shares refused (ring
+                                full), idle polls */
   int64_t* stats;            /* device [num_instances*SCUBA_NSTATS], added to; may
                                 be NULL. Per instance: decisions, conflicts,
                                 propagations (trail literals processed),

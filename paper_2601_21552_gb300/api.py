@@ -47,10 +47,11 @@ class DeviceBatch:
 
 def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
             time_budget_ms: int = 0, split: bool = True, warps_per_block: int = 0,
-            blocks_per_sm: int = 0, split_interval: int = 0, stats: torch.Tensor | None = None,
+            blocks_per_sm: int = 0, split_interval: int = 0, split_min: int = 0, trail_placement: int = 0, stats: torch.Tensor | None = None,
             order: torch.Tensor | None = None, mlp_weights: torch.Tensor | None = None,
             learned_depth: int = 0, abort_flag_ptr: int | None = None,
-            events: tuple | None = None) -> B.scuba_options:
+            events: tuple | None = None, finish_ns: torch.Tensor | None = None,
+            profile: torch.Tensor | None = None) -> B.scuba_options:
     o = B.scuba_options_init()
     o.heuristic = heuristic
     o.decision_budget = decision_budget
@@ -59,11 +60,15 @@ def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
     o.warps_per_block = warps_per_block
     o.blocks_per_sm = blocks_per_sm
     o.split_interval = split_interval
+    o.split_min = split_min
+    o.trail_placement = trail_placement
     o.stats = stats.data_ptr() if stats is not None else None
     o.order = order.data_ptr() if order is not None else None
     o.mlp_weights = mlp_weights.data_ptr() if mlp_weights is not None else None
     o.learned_depth = learned_depth
     o.abort_flag = abort_flag_ptr
+    o.finish_ns = finish_ns.data_ptr() if finish_ns is not None else None
+    o.profile = profile.data_ptr() if profile is not None else None
     if events is not None:
         o.search_event_begin = events[0].cuda_event
         o.search_event_end = events[1].cuda_event

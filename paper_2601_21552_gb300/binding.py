@@ -43,6 +43,8 @@ class scuba_options(ctypes.Structure):
     _fields_ = [("heuristic", _i32), ("learned_depth", _i32), ("mlp_weights", _vp),
                 ("decision_budget", _i64), ("time_budget_ms", _i64), ("split", _i32),
                 ("warps_per_block", _i32), ("blocks_per_sm", _i32), ("split_interval", _i32),
+                ("split_min", _i32), ("trail_placement", _i32), ("finish_ns", _vp),
+                ("profile", _vp),
                 ("stats", _vp), ("order", _vp), ("abort_flag", _vp),
                 ("search_event_begin", _vp), ("search_event_end", _vp)]
 

@@ -328,7 +328,7 @@ struct Job {            // a DPLL subtree: the instance plus assumed literals
   int32_t len;
   uint32_t lit[MAX_PREFIX];
   uint32_t seq;         // ring-buffer sequence number (Vyukov MPMC queue)
-  uint32_t pad[1];
+  float inc;            // donor's activity increment; its activities are in job_act
 };
 
 struct Solve {
@@ -360,13 +360,19 @@ struct Solve {
   float* act;
   // job ring
   Job* ring;
+  float* job_act;          // [ring_cap x vmax] donor activity snapshot per cell
+  uint32_t* prefix;        // [slots x MAX_PREFIX] the running job's assumptions
   uint32_t ring_cap;       // power of two
+  int32_t split_min;       // decisions a job makes before it may donate
   Ctrl* ctrl;
   int64_t budget;
   uint64_t time_ns;
   const volatile int32_t* abort_flag;
   int split;
   int split_interval;
+  int trail_smem;          // 1: each warp's trail lives in shared memory
+  int64_t* finish_ns;      // optional [n]: completion time of each instance
+  unsigned long long* prof;  // optional [8]: search counters
 };
 
 struct WarpShared {
@@ -659,9 +665,13 @@ __device__ bool ring_push(const Solve& S, const Warp& w, int inst, uint32_t plen
     if (k == flip_index) lit ^= 1u;
     cell->lit[k] = lit;
   }
+  // the thief continues with the donor's activity ordering
+  float* snap = S.job_act + (size_t)(slot & (S.ring_cap - 1)) * S.vmax;
+  for (uint32_t v = w.lane; v < w.V; v += 32) snap[v] = w.act[v];
   if (w.lane == 0) {
     cell->inst = inst;
     cell->len = (int32_t)plen;
+    cell->inc = w.inc;
   }
   __threadfence();
   __syncwarp();
@@ -717,7 +727,9 @@ __device__ void finish_job(const Solve& S, Warp& w, int inst, int r) {
       uint32_t d = atomicOr(&S.done[inst], 4u);
       if (!(d & 1u)) S.verdict[inst] = (d & 2u) ? SCUBA_UNKNOWN : SCUBA_UNSAT;
       atomicSub(&S.ctrl->inst_left, 1u);
+      if (S.finish_ns) S.finish_ns[inst] = (int64_t)(globaltimer() - S.ctrl->t0);
     }
+    if (S.prof) atomicAdd(&S.prof[1], 1ull);  // jobs run
     if (S.stats) {
       unsigned long long* st = (unsigned long long*)&S.stats[SCUBA_NSTATS * (int64_t)inst];
       atomicAdd(st + 0, (unsigned long long)w.decisions);
@@ -732,7 +744,15 @@ __device__ void finish_job(const Solve& S, Warp& w, int inst, int r) {
 }
 
 // Solve one subtree (inst + assumptions). Returns SAT / UNSAT / UNKNOWN.
-__device__ int run_job(const Solve& S, Warp& w, int inst, const Job* job, int& abort_code) {
+// A taken job (a shared subtree) in slot-private memory: the ring cell is
+// released as soon as it has been copied.
+struct TakenJob {
+  const uint32_t* lit;  // assumptions, in order
+  int32_t len;
+  float inc;            // activities were copied into the warp's act[] already
+};
+
+__device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, int& abort_code) {
   w.inst = inst;
   w.V = (uint32_t)S.nv[inst];
   w.c0 = S.icb[inst];
@@ -746,7 +766,11 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const Job* job, int& a
   w.decisions = w.conflicts = w.props = w.visits = w.act_reads = w.undone = 0;
   const uint32_t nwords = (w.V + 15u) >> 4;
   for (uint32_t k = w.lane; k < nwords; k += 32) w.asg[k] = 0u;
-  for (uint32_t v = w.lane; v < w.V; v += 32) w.act[v] = 0.0f;
+  if (job) {
+    w.inc = job->inc;
+  } else {
+    for (uint32_t v = w.lane; v < w.V; v += 32) w.act[v] = 0.0f;
+  }
   if (w.lane == 0) {
     w.ws->tail = 0;
     w.ws->conflict = 0;
@@ -819,7 +843,8 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const Job* job, int& a
       if ((int64_t)tot >= S.budget) return SCUBA_UNKNOWN;
     }
     // share the untried branch of the shallowest open decision
-    if (S.split && (w.decisions % S.split_interval) == 0 && w.nd > w.nd_fixed) {
+    if (S.split && w.decisions >= S.split_min && (w.decisions % S.split_interval) == 0 &&
+        w.nd > w.nd_fixed) {
       uint32_t idle = 0;
       if (w.lane == 0) idle = *(volatile uint32_t*)&S.ctrl->idle;
       idle = __shfl_sync(FULL, idle, 0);
@@ -835,9 +860,15 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const Job* job, int& a
             if (w.lane == 0) {
               w.dstack[k] |= FLIP;
               atomicAdd(&S.ctrl->jobs_split, 1u);
+              if (S.prof) {
+                atomicAdd(&S.prof[0], 1ull);                       // jobs shared
+                atomicAdd(&S.prof[2], (unsigned long long)(k + 1)); // prefix literals
+                atomicAdd(&S.prof[3], (unsigned long long)(w.nd - k)); // depth left
+              }
             }
           } else if (w.lane == 0) {
             atomicSub(&S.pending[inst], 1u);
+            if (S.prof) atomicAdd(&S.prof[4], 1ull);  // ring full
           }
           __syncwarp();
         }
@@ -864,7 +895,10 @@ __global__ void __launch_bounds__(256) k_solve(Solve S) {
   w.S = &S;
   w.ws = &wsh[wib];
   w.asg = smem + (sizeof(WarpShared) / 4) * wpb + (size_t)S.assign_words * wib;
-  w.trail = S.trail + slot * S.vmax;
+  w.trail = S.trail_smem
+                ? smem + (sizeof(WarpShared) / 4) * wpb + (size_t)S.assign_words * wpb +
+                      (size_t)S.vmax * wib
+                : S.trail + slot * S.vmax;
   w.dstack = S.dstack + slot * S.vmax;
   w.act = S.act + slot * S.vmax;
   w.lane = lane;
@@ -874,10 +908,24 @@ __global__ void __launch_bounds__(256) k_solve(Solve S) {
     // 1) a shared subtree, 2) a fresh instance, 3) wait for shared work
     int inst = -1;
     uint32_t slot_j = ring_pop(S, lane);
-    const Job* job = nullptr;
+    TakenJob taken;
+    const TakenJob* job = nullptr;
     if (slot_j != NONE) {
-      job = &S.ring[slot_j & (S.ring_cap - 1)];
-      inst = job->inst;
+      // copy the cell out (prefix, activity snapshot) and release it at once
+      const Job* cell = &S.ring[slot_j & (S.ring_cap - 1)];
+      inst = cell->inst;
+      const int32_t len = cell->len;
+      uint32_t* pre = S.prefix + slot * MAX_PREFIX;
+      for (int k = lane; k < len; k += 32) pre[k] = cell->lit[k];
+      const float* snap = S.job_act + (size_t)(slot_j & (S.ring_cap - 1)) * S.vmax;
+      const int32_t V = min(S.nv[inst], S.vmax);
+      for (int v = lane; v < V; v += 32) w.act[v] = snap[v];
+      taken.lit = pre;
+      taken.len = len;
+      taken.inc = cell->inc;
+      __syncwarp();
+      ring_release(S, slot_j, lane);
+      job = &taken;
     } else {
       uint32_t k = 0;
       if (lane == 0) k = atomicAdd(&S.ctrl->next_inst, 1u);
@@ -895,7 +943,10 @@ __global__ void __launch_bounds__(256) k_solve(Solve S) {
           else if (*(volatile int32_t*)&S.ctrl->status != 0) stop = 1;
           else if (S.abort_flag && *S.abort_flag) { stop = 1; set_status(S, SCUBA_ERR_ABORTED); }
           else if (globaltimer() - S.ctrl->t0 > S.time_ns) { stop = 1; set_status(S, SCUBA_ERR_TIMEOUT); }
-          else __nanosleep(2000);
+          else {
+            if (S.prof) atomicAdd(&S.prof[5], 1ull);  // idle polls
+            __nanosleep(2000);
+          }
         }
         stop = __shfl_sync(FULL, stop, 0);
         if (stop) break;
@@ -923,7 +974,6 @@ __global__ void __launch_bounds__(256) k_solve(Solve S) {
     } else {
       r = run_job(S, w, inst, job, abort_code);
     }
-    if (job) ring_release(S, slot_j, lane);
     finish_job(S, w, inst, r);
     if (abort_code) {
       if (lane == 0) set_status(S, abort_code);
@@ -982,7 +1032,7 @@ struct Buf {
 
 struct Scratch {
   Buf occ_base, norm, occ_cnt, occ_begin, ent, units, nunits, flags;
-  Buf pending, done, inst_dec, trail, dstack, act, ring, ctrl;
+  Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
   int32_t last_status = 0;
@@ -1080,24 +1130,32 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   // occurrence offsets: sum over instances of (2V+1)
   const int64_t occ_total = 2LL * b->total_vars + n;
 
-  // shape: warps per block x blocks per SM (shared memory bounds the warps)
+  // shape: warps per block x blocks per SM (shared memory bounds the warps).
+  // The trail goes to shared memory when that still leaves >= 16 warps/SM.
   int wpb = opt->warps_per_block > 0 ? opt->warps_per_block : 8;
   int bps = opt->blocks_per_sm > 0 ? opt->blocks_per_sm : 4;
   wpb = std::min(wpb, 8);
   const uint32_t assign_words = (uint32_t)((vmax + 15) / 16);
-  size_t smem = (sizeof(dev::WarpShared) + (size_t)assign_words * 4) * wpb;
-  const size_t smem_cap = 227 * 1024;
+  const size_t smem_cap = 227 * 1024, sm_cap = 228 * 1024;
+  const size_t per_warp_g = sizeof(dev::WarpShared) + (size_t)assign_words * 4;
+  const size_t per_warp_s = per_warp_g + (size_t)vmax * 4;
+  // Global memory by default: a small shared-memory carve-out leaves a larger L1
+  // for the read-only occurrence lists, which measured faster.
+  int trail_smem = opt->trail_placement == 1 ? 1 : 0;
+  (void)per_warp_s;
+  size_t per_warp = trail_smem ? per_warp_s : per_warp_g;
+  size_t smem = per_warp * wpb;
   while (wpb > 1 && smem > smem_cap) {
     wpb--;
-    smem = (sizeof(dev::WarpShared) + (size_t)assign_words * 4) * wpb;
+    smem = per_warp * wpb;
   }
   if (smem > smem_cap) {
-    set_error("scuba_solve_batch: instance too large for shared-memory assignment");
+    set_error("scuba_solve_batch: instance too large for the shared-memory assignment");
     return SCUBA_ERR_TOO_LARGE;
   }
-  while (bps > 1 && smem * bps > 228 * 1024) bps--;
+  while (bps > 1 && (smem + 1024) * bps > sm_cap) bps--;
   const int64_t slots = (int64_t)S.sms * bps * wpb;
-  const uint32_t ring_cap = 4096;
+  const uint32_t ring_cap = 2048;
 
   if (ensure(S.occ_base, 8 * (size_t)(n + 1)) || ensure(S.norm, 4 * (size_t)L) ||
       ensure(S.occ_cnt, 4 * (size_t)occ_total) || ensure(S.occ_begin, 4 * (size_t)occ_total) ||
@@ -1106,7 +1164,9 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
       ensure(S.pending, 4 * (size_t)n) || ensure(S.done, 4 * (size_t)n) ||
       ensure(S.inst_dec, 8 * (size_t)n) || ensure(S.trail, 4 * (size_t)slots * vmax) ||
       ensure(S.dstack, 4 * (size_t)slots * vmax) || ensure(S.act, 4 * (size_t)slots * vmax) ||
-      ensure(S.ring, sizeof(dev::Job) * (size_t)ring_cap) || ensure(S.ctrl, sizeof(dev::Ctrl))) {
+      ensure(S.ring, sizeof(dev::Job) * (size_t)ring_cap) ||
+      ensure(S.job_act, 4 * (size_t)ring_cap * vmax) ||
+      ensure(S.prefix, 4 * (size_t)slots * dev::MAX_PREFIX) || ensure(S.ctrl, sizeof(dev::Ctrl))) {
     set_error("scuba_solve_batch: out of device memory for scratch");
     return SCUBA_ERR_NOMEM;
   }
@@ -1171,6 +1231,9 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.act = P<float>(S.act);
   sv.ring = P<dev::Job>(S.ring);
   sv.ring_cap = ring_cap;
+  sv.job_act = P<float>(S.job_act);
+  sv.prefix = P<uint32_t>(S.prefix);
+  sv.split_min = opt->split_min > 0 ? opt->split_min : 256;
   sv.ctrl = P<dev::Ctrl>(S.ctrl);
   sv.budget = opt->decision_budget;
   int64_t tb = opt->time_budget_ms > 0 ? opt->time_budget_ms : 600000;
@@ -1178,6 +1241,9 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.abort_flag = opt->abort_flag;
   sv.split = opt->split ? 1 : 0;
   sv.split_interval = opt->split_interval > 0 ? opt->split_interval : 16;
+  sv.trail_smem = trail_smem;
+  sv.finish_ns = opt->finish_ns;
+  sv.prof = reinterpret_cast<unsigned long long*>(opt->profile);
 
   dev::k_init_ring<<<16, 256, 0, st>>>(sv.ring, ring_cap);
   dev::k_init_inst<<<(n + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec, n);
@@ -1274,7 +1340,7 @@ extern "C" void scuba_release(void) {
   Scratch& S = it->second;
   Buf* all[] = {&S.occ_base, &S.norm, &S.occ_cnt, &S.occ_begin, &S.ent, &S.units, &S.nunits,
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
-                &S.ring, &S.ctrl, &S.h_icb, &S.h_cb, &S.h_lits, &S.h_nv, &S.h_vb,
+                &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.h_icb, &S.h_cb, &S.h_lits, &S.h_nv, &S.h_vb,
                 &S.h_verdict, &S.h_model, &S.h_stats};
   for (Buf* x : all) {
     if (x->p) cudaFree(x->p);
