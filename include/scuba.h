@@ -155,6 +155,10 @@ const char* scuba_last_error(void);
 /* Library ABI version (monotonic integer). */
 int scuba_version(void);
 
+/* out[2] = {sizeof(scuba_cnf_batch), sizeof(scuba_options)} as compiled into
+   the library, so bindings can check their struct layouts. */
+int scuba_abi_sizes(int64_t* out);
+
 /* ------------------------------------------------------------------------- */
 /* Host side: query encoding and model re-verification                        */
 /* ------------------------------------------------------------------------- */

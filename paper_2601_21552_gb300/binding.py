@@ -70,6 +70,7 @@ _sig("scuba_sync_status", _i32, [_vp])
 _sig("scuba_release", None, [])
 _sig("scuba_last_error", ctypes.c_char_p, [])
 _sig("scuba_version", _i32, [])
+_sig("scuba_abi_sizes", _i32, [_vp])
 _sig("scuba_encode_batch", _i32, [_i32, _vp, _vp, _i32, ctypes.POINTER(_vp)])
 _sig("scuba_encoded_sizes", _i32, [_vp, _vp])
 _sig("scuba_encoded_copy", _i32, [_vp, _vp, _vp, _vp, _vp, _vp])
@@ -80,13 +81,24 @@ _sig("scuba_verify_batch", _i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp])
 EXPORTED = [
     "scuba_options_init", "scuba_solve_batch", "scuba_solve_batch_ex",
     "scuba_solve_batch_host", "scuba_sync_status", "scuba_release", "scuba_last_error",
-    "scuba_version", "scuba_encode_batch", "scuba_encoded_sizes", "scuba_encoded_copy",
+    "scuba_version", "scuba_abi_sizes", "scuba_encode_batch", "scuba_encoded_sizes", "scuba_encoded_copy",
     "scuba_encoded_inputs", "scuba_encoded_free", "scuba_verify_batch",
 ]
 
 
 def _np_ptr(a: np.ndarray):
     return a.ctypes.data_as(_vp)
+
+
+def _check_layout():
+    sz = np.zeros(2, dtype=np.int64)
+    _lib.scuba_abi_sizes(_np_ptr(sz))
+    mine = (ctypes.sizeof(scuba_cnf_batch), ctypes.sizeof(scuba_options))
+    if tuple(int(x) for x in sz) != mine:
+        raise ImportError(f"libscuba struct layout {tuple(sz)} != binding {mine}; rebuild")
+
+
+_check_layout()
 
 
 def last_error() -> str:

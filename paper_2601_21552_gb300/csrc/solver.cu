@@ -380,6 +380,8 @@ struct WarpShared {
   uint32_t conflict;
   uint32_t cl[3];
   uint32_t pad[3];
+  // per-job work counters (lane 0 updates them; kept out of registers)
+  unsigned long long decisions, conflicts, props, visits, act_reads, undone;
 };
 
 enum : uint32_t { LV_U = 0, LV_T = 1, LV_F = 2, LV_X = 3 };
@@ -410,8 +412,13 @@ struct Warp {
   uint32_t nd;
   uint32_t nd_fixed;       // decisions below this index are assumptions
   float inc;
-  int64_t decisions, conflicts, props, visits, act_reads, undone;
+  uint32_t decisions;      // decisions of the current job
 };
+
+#define WCOUNT(w, field, amount)                 \
+  do {                                           \
+    if ((w).lane == 0) (w).ws->field += (amount); \
+  } while (0)
 
 __device__ __forceinline__ void record_conflict(Warp& w, uint32_t a, uint32_t b, uint32_t c) {
   if (atomicCAS(&w.ws->conflict, 0u, 1u) == 0u) {
@@ -485,6 +492,8 @@ __device__ __forceinline__ void eval_entry(Warp& w, uint32_t f, uint64_t e) {
 }
 
 // Unit propagation to a fixpoint. Returns true on conflict.
+// Each round takes the trail literals assigned in the previous round (the
+// frontier) and spreads their occurrence entries over the 32 lanes.
 __device__ bool bcp(Warp& w) {
   for (;;) {
     __syncwarp();
@@ -492,41 +501,66 @@ __device__ bool bcp(Warp& w) {
     if (w.head >= hi) return false;
     const uint32_t lo = w.head;
     w.head = hi;
-    w.props += hi - lo;
+    WCOUNT(w, props, hi - lo);
     for (uint32_t base = lo; base < hi; base += 32) {
-      const uint32_t t = base + w.lane;
-      uint32_t f = 0, beg = 0, cnt = 0;
-      if (t < hi) {
-        f = w.trail[t] ^ 1u;              // the literal that became false
-        beg = __ldg(&w.occ[f]);
-        cnt = __ldg(&w.occ[f + 1]) - beg;
-      }
-      uint32_t inc = cnt;
-      for (int d = 1; d < 32; d <<= 1) {
-        uint32_t y = __shfl_up_sync(FULL, inc, d);
-        if (w.lane >= d) inc += y;
-      }
-      const uint32_t total = __shfl_sync(FULL, inc, 31);
-      w.visits += total;
-      for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-        const uint32_t e = e0 + w.lane;
-        // owner = smallest lane j with inc_j > e
-        int lo_j = 0, hi_j = 31;
-#pragma unroll
-        for (int s = 0; s < 5; s++) {
-          int mid = (lo_j + hi_j) >> 1;
-          uint32_t v = __shfl_sync(FULL, inc, mid);
-          if (v > e) hi_j = mid; else lo_j = mid + 1;
-          if (lo_j > hi_j) lo_j = hi_j;
+      const uint32_t nlit = min(32u, hi - base);
+      if (nlit == 1) {
+        // one literal: every lane reads the same list bounds (broadcast)
+        const uint32_t f = w.trail[base] ^ 1u;
+        const uint32_t beg = __ldg(&w.occ[f]);
+        const uint32_t cnt = __ldg(&w.occ[f + 1]) - beg;
+        WCOUNT(w, visits, cnt);
+        for (uint32_t e = w.lane; e < cnt; e += 32) eval_entry(w, f, __ldg(&w.ent[beg + e]));
+      } else {
+        uint32_t f = 0, beg = 0, cnt = 0;
+        if (w.lane < nlit) {
+          f = w.trail[base + w.lane] ^ 1u;  // the literal that became false
+          beg = __ldg(&w.occ[f]);
+          cnt = __ldg(&w.occ[f + 1]) - beg;
         }
-        const int j = lo_j;
-        const uint32_t jinc = __shfl_sync(FULL, inc, j);
-        const uint32_t jcnt = __shfl_sync(FULL, cnt, j);
-        const uint32_t jbeg = __shfl_sync(FULL, beg, j);
-        const uint32_t jf = __shfl_sync(FULL, f, j);
-        if (e < total) {
-          const uint64_t en = __ldg(&w.ent[jbeg + (e - (jinc - jcnt))]);
-          eval_entry(w, jf, en);
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          uint32_t y = __shfl_up_sync(FULL, inc, d);
+          if (w.lane >= d) inc += y;
+        }
+        const uint32_t excl = inc - cnt;
+        const uint32_t total = __shfl_sync(FULL, inc, 31);
+        WCOUNT(w, visits, total);
+        if (total <= 32) {
+          // owner of entry e = the lane whose segment starts at the last
+          // segment start <= e: segment starts as a bit mask, ranks by popc
+          const bool has = cnt > 0;
+          const uint32_t starts = __reduce_or_sync(FULL, has ? (1u << excl) : 0u);
+          const uint32_t nz = __ballot_sync(FULL, has);
+          const uint32_t e = w.lane;
+          int j = 0;
+          if (e < total) {
+            const int rank = __popc(starts & ((2u << e) - 1u)) - 1;
+            j = __fns(nz, 0, rank + 1);
+          }
+          const uint32_t jbeg = __shfl_sync(FULL, beg, j);
+          const uint32_t jex = __shfl_sync(FULL, excl, j);
+          const uint32_t jf = __shfl_sync(FULL, f, j);
+          if (e < total) eval_entry(w, jf, __ldg(&w.ent[jbeg + (e - jex)]));
+        } else {
+          for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+            const uint32_t e = e0 + w.lane;
+            // owner = smallest lane j with inc_j > e
+            int lo_j = 0, hi_j = 31;
+#pragma unroll
+            for (int s2 = 0; s2 < 5; s2++) {
+              int mid = (lo_j + hi_j) >> 1;
+              uint32_t v = __shfl_sync(FULL, inc, mid);
+              if (v > e) hi_j = mid; else lo_j = mid + 1;
+              if (lo_j > hi_j) lo_j = hi_j;
+            }
+            const int j = lo_j;
+            const uint32_t jbeg = __shfl_sync(FULL, beg, j);
+            const uint32_t jex = __shfl_sync(FULL, excl, j);
+            const uint32_t jf = __shfl_sync(FULL, f, j);
+            if (e < total) eval_entry(w, jf, __ldg(&w.ent[jbeg + (e - jex)]));
+          }
         }
       }
       __syncwarp();
@@ -579,7 +613,7 @@ __device__ bool backtrack(Warp& w) {
   const uint32_t pos = w.dstack[nd - 1] & ~FLIP;
   const uint32_t tail = *(volatile uint32_t*)&w.ws->tail;
   const uint32_t d = w.trail[pos];
-  w.undone += tail - pos;
+  WCOUNT(w, undone, tail - pos);
   for (uint32_t t = pos + w.lane; t < tail; t += 32) {
     uint32_t v = w.trail[t] >> 1;
     atomicAnd(&w.asg[v >> 4], ~(3u << ((v & 15u) * 2u)));
@@ -732,12 +766,12 @@ __device__ void finish_job(const Solve& S, Warp& w, int inst, int r) {
     if (S.prof) atomicAdd(&S.prof[1], 1ull);  // jobs run
     if (S.stats) {
       unsigned long long* st = (unsigned long long*)&S.stats[SCUBA_NSTATS * (int64_t)inst];
-      atomicAdd(st + 0, (unsigned long long)w.decisions);
-      atomicAdd(st + 1, (unsigned long long)w.conflicts);
-      atomicAdd(st + 2, (unsigned long long)w.props);
-      atomicAdd(st + 3, (unsigned long long)w.visits);
-      atomicAdd(st + 4, (unsigned long long)w.act_reads);
-      atomicAdd(st + 5, (unsigned long long)w.undone);
+      atomicAdd(st + 0, w.ws->decisions);
+      atomicAdd(st + 1, w.ws->conflicts);
+      atomicAdd(st + 2, w.ws->props);
+      atomicAdd(st + 3, w.ws->visits);
+      atomicAdd(st + 4, w.ws->act_reads);
+      atomicAdd(st + 5, w.ws->undone);
     }
   }
   __syncwarp();
@@ -763,7 +797,6 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, i
   w.nd = 0;
   w.nd_fixed = 0;
   w.inc = 1.0f;
-  w.decisions = w.conflicts = w.props = w.visits = w.act_reads = w.undone = 0;
   const uint32_t nwords = (w.V + 15u) >> 4;
   for (uint32_t k = w.lane; k < nwords; k += 32) w.asg[k] = 0u;
   if (job) {
@@ -815,12 +848,12 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, i
       if (stop == 3) return SCUBA_UNSAT;  // the instance is SAT already; this subtree is moot
     }
     if (bcp(w)) {
-      w.conflicts++;
+      WCOUNT(w, conflicts, 1);
       bump(w);
       if (!backtrack(w)) return SCUBA_UNSAT;
       continue;
     }
-    w.act_reads += w.V - *(volatile uint32_t*)&w.ws->tail;
+    WCOUNT(w, act_reads, w.V - *(volatile uint32_t*)&w.ws->tail);
     const uint32_t v = pick(w);
     if (v == NONE) {
       // the first subtree of the instance to reach a model writes it
@@ -875,6 +908,7 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, i
       }
     }
     w.decisions++;
+    WCOUNT(w, decisions, 1);
     if (w.lane == 0) {
       w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
       imply(w, 2u * v + 1u);  // false first
@@ -884,7 +918,8 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, i
   }
 }
 
-__global__ void __launch_bounds__(256) k_solve(Solve S) {
+// 48 registers per thread: 5 blocks x 8 warps = 40 resident warps per SM
+__global__ void __launch_bounds__(256, 5) k_solve(const __grid_constant__ Solve S) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -959,7 +994,12 @@ __global__ void __launch_bounds__(256) k_solve(Solve S) {
     }
     int abort_code = 0;
     int r;
-    w.decisions = w.conflicts = w.props = w.visits = w.act_reads = w.undone = 0;
+    w.decisions = 0;
+    if (lane == 0) {
+      w.ws->decisions = w.ws->conflicts = w.ws->props = 0;
+      w.ws->visits = w.ws->act_reads = w.ws->undone = 0;
+    }
+    __syncwarp();
     uint32_t moot = 0;
     if (lane == 0) moot = *(volatile uint32_t*)&S.done[inst] & 1u;
     moot = __shfl_sync(FULL, moot, 0);
@@ -1076,6 +1116,13 @@ int cuda_fail(const char* what, cudaError_t e) {
 
 using namespace scuba;
 
+extern "C" int scuba_abi_sizes(int64_t* out) {
+  if (!out) return SCUBA_ERR_ARG;
+  out[0] = (int64_t)sizeof(scuba_cnf_batch);
+  out[1] = (int64_t)sizeof(scuba_options);
+  return SCUBA_OK;
+}
+
 extern "C" int scuba_options_init(scuba_options* o) {
   if (!o) return SCUBA_ERR_ARG;
   std::memset(o, 0, sizeof(*o));
@@ -1133,7 +1180,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   // shape: warps per block x blocks per SM (shared memory bounds the warps).
   // The trail goes to shared memory when that still leaves >= 16 warps/SM.
   int wpb = opt->warps_per_block > 0 ? opt->warps_per_block : 8;
-  int bps = opt->blocks_per_sm > 0 ? opt->blocks_per_sm : 4;
+  int bps = opt->blocks_per_sm > 0 ? opt->blocks_per_sm : 5;
   wpb = std::min(wpb, 8);
   const uint32_t assign_words = (uint32_t)((vmax + 15) / 16);
   const size_t smem_cap = 227 * 1024, sm_cap = 228 * 1024;
