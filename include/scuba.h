@@ -143,6 +143,33 @@ int scuba_solve_batch_ex(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t
 int scuba_solve_batch_host(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t* model,
                            void* stream, const scuba_options* opt);
 
+/*
+ * Allocation-free variant of scuba_solve_batch_ex (the paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc, such as
+ * code running under another framework's allocator or a plugin host that
+ * forbids device allocation). It runs the same preparation and search
+ * kernels, but every scratch buffer is carved from one fixed 64 MiB array in
+ * device global memory that the library declares statically; every GPU that
+ * loads the library holds that array until the process exits. The call makes
+ * no device allocation (no cudaMalloc/cudaFree, no allocating library call).
+ *   - Arguments as for scuba_solve_batch_ex (device pointers); only
+ *     SCUBA_HEUR_ACTIVITY; profiling outputs and search events are ignored.
+ *   - Shape: one block of 4 warps per SM and a 256-job subtree ring, so a
+ *     batch fits when its scratch (about 12*L + 8*(2*total_vars + n) + 12*C
+ *     bytes plus 12*max_vars per warp) is at most 64 MiB; larger batches are
+ *     rejected with SCUBA_ERR_TOO_LARGE and a message naming the limit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - The call waits for `stream` and returns the device-side status itself.
+ *   - All calls share the one array and it keeps the previous call's contents
+ *     (everything that must start at zero is cleared by the call). Calls that
+ *     overlap on the GPU -- on different streams, or from different host
+ *     threads -- race on that array and must not be issued.
+ */
+int scuba_solve_batch_noalloc(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t* model,
+                              void* stream, const scuba_options* opt);
+
 /* Waits for `stream` and returns the status of the last solve issued on it. */
 int scuba_sync_status(void* stream);
 

@@ -66,6 +66,8 @@ _sig("scuba_solve_batch_ex", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _
                                     ctypes.POINTER(scuba_options)])
 _sig("scuba_solve_batch_host", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _vp,
                                       ctypes.POINTER(scuba_options)])
+_sig("scuba_solve_batch_noalloc", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _vp,
+                                         ctypes.POINTER(scuba_options)])
 _sig("scuba_sync_status", _i32, [_vp])
 _sig("scuba_release", None, [])
 _sig("scuba_last_error", ctypes.c_char_p, [])
@@ -80,7 +82,7 @@ _sig("scuba_verify_batch", _i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp])
 
 EXPORTED = [
     "scuba_options_init", "scuba_solve_batch", "scuba_solve_batch_ex",
-    "scuba_solve_batch_host", "scuba_sync_status", "scuba_release", "scuba_last_error",
+    "scuba_solve_batch_host", "scuba_solve_batch_noalloc", "scuba_sync_status", "scuba_release", "scuba_last_error",
     "scuba_version", "scuba_abi_sizes", "scuba_encode_batch", "scuba_encoded_sizes", "scuba_encoded_copy",
     "scuba_encoded_inputs", "scuba_encoded_free", "scuba_verify_batch",
 ]
@@ -227,6 +229,17 @@ def scuba_solve_batch_host(batch: scuba_cnf_batch, verdict: np.ndarray, model,
     return _lib.scuba_solve_batch_host(ctypes.byref(batch), _np_ptr(verdict),
                                        _np_ptr(model) if model is not None else None,
                                        stream_ptr, ctypes.byref(opt))
+
+
+def scuba_solve_batch_noalloc(batch: scuba_cnf_batch, verdict_ptr: int, model_ptr, stream_ptr,
+                              opt: scuba_options | None = None) -> int:
+    """Allocation-free solve (fixed static scratch); waits and returns the
+    device status. Raises on argument/size errors like the other calls."""
+    if opt is None:
+        opt = scuba_options_init()
+    return _check(_lib.scuba_solve_batch_noalloc(ctypes.byref(batch), verdict_ptr, model_ptr,
+                                                 stream_ptr, ctypes.byref(opt)),
+                  "scuba_solve_batch_noalloc")
 
 
 def scuba_sync_status(stream_ptr=None) -> int:

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -1395,4 +1396,215 @@ extern "C" void scuba_release(void) {
     x->cap = 0;
   }
   scratch_map().erase(it);
+}
+
+// --------------------------------------------------------------------------
+// Allocation-free variant
+//
+// Some callers cannot call cudaMalloc: code that runs inside another
+// framework's memory pool or allocator hooks, inside a plugin whose host
+// forbids device allocation, or on a path where a synchronous allocation would
+// stall other streams. For them scuba_solve_batch_noalloc runs the same
+// preparation and search kernels with every scratch buffer carved out of one
+// file-scope device array of fixed size. Every GPU that loads this library
+// holds that array until the process exits.
+// --------------------------------------------------------------------------
+
+namespace scuba {
+namespace {
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB
+constexpr int kNoAllocWarpsPerBlock = 4;
+constexpr uint32_t kNoAllocRingCap = 256;
+constexpr int kMaxDevices = 256;
+void* g_noalloc_scratch_addr[kMaxDevices];  // device address of the array, per device
+}  // namespace
+}  // namespace scuba
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[scuba::kNoAllocScratchBytes];
+
+extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verdict,
+                                         uint8_t* model, void* stream,
+                                         const scuba_options* opt) {
+  using namespace scuba;
+  if (!b || b->num_instances < 0 || b->total_clauses < 0 || b->total_lits < 0 ||
+      b->max_vars < 0 || b->total_vars < 0) {
+    set_error("scuba_solve_batch_noalloc: bad arguments");
+    return SCUBA_ERR_ARG;
+  }
+  scuba_options defaults;
+  scuba_options_init(&defaults);
+  if (!opt) opt = &defaults;
+  const int n = b->num_instances;
+  if (n == 0) return SCUBA_OK;
+  if (!verdict || !b->inst_clause_begin || !b->clause_begin || !b->inst_num_vars ||
+      !b->inst_var_begin || (b->total_lits > 0 && !b->lits)) {
+    set_error("scuba_solve_batch_noalloc: NULL array");
+    return SCUBA_ERR_ARG;
+  }
+  if (opt->heuristic != SCUBA_HEUR_ACTIVITY) {
+    set_error("scuba_solve_batch_noalloc: only activity branching is supported");
+    return SCUBA_ERR_ARG;
+  }
+  if (b->max_vars >= (1 << 29) || b->total_lits >= (1LL << 32)) {
+    set_error("scuba_solve_batch_noalloc: instance too large");
+    return SCUBA_ERR_TOO_LARGE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("scuba_solve_batch_noalloc: device ordinal out of range");
+    return SCUBA_ERR_ARG;
+  }
+  // set-up, once per device, with that device current: the host-side name of
+  // the array is not a device address, so ask the runtime for it
+  if (!g_noalloc_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail("cudaGetSymbolAddress", e);
+    g_noalloc_scratch_addr[dev] = p;
+  }
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail("cudaDeviceGetAttribute", e);
+
+  const int64_t C = b->total_clauses, L = b->total_lits;
+  const int vmax = std::max(1, (int)b->max_vars);
+  const int64_t occ_total = 2LL * b->total_vars + n;
+  const int wpb = kNoAllocWarpsPerBlock;
+  const uint32_t assign_words = (uint32_t)((vmax + 15) / 16);
+  const size_t smem = (sizeof(dev::WarpShared) + (size_t)assign_words * 4) * wpb;
+  if (smem > 227 * 1024) {
+    set_error("scuba_solve_batch_noalloc: instance too large for the shared-memory assignment");
+    return SCUBA_ERR_TOO_LARGE;
+  }
+  const int64_t slots = (int64_t)sms * wpb;  // one block per SM
+  const uint32_t ring_cap = kNoAllocRingCap;
+
+  // carve every buffer out of the static array, 256-byte aligned
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t at = off;
+    off += (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t o_occ_base = carve(8 * (size_t)(n + 1)), o_norm = carve(4 * (size_t)L),
+               o_occ_cnt = carve(4 * (size_t)occ_total), o_occ_begin = carve(4 * (size_t)occ_total),
+               o_ent = carve(8 * (size_t)L), o_units = carve(4 * (size_t)std::max<int64_t>(C, 1)),
+               o_nunits = carve(4 * (size_t)n), o_flags = carve(4 * (size_t)n),
+               o_pending = carve(4 * (size_t)n), o_done = carve(4 * (size_t)n),
+               o_inst_dec = carve(8 * (size_t)n), o_trail = carve(4 * (size_t)slots * vmax),
+               o_dstack = carve(4 * (size_t)slots * vmax), o_act = carve(4 * (size_t)slots * vmax),
+               o_ring = carve(sizeof(dev::Job) * (size_t)ring_cap),
+               o_job_act = carve(4 * (size_t)ring_cap * vmax),
+               o_prefix = carve(4 * (size_t)slots * dev::MAX_PREFIX),
+               o_ctrl = carve(sizeof(dev::Ctrl));
+  if (off > kNoAllocScratchBytes) {
+    set_error("scuba_solve_batch_noalloc: batch needs " + std::to_string(off) +
+              " bytes of scratch, more than the fixed " +
+              std::to_string(kNoAllocScratchBytes) + " bytes");
+    return SCUBA_ERR_TOO_LARGE;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_scratch_addr[dev]);
+  auto at = [&](size_t o) { return static_cast<void*>(base + o); };
+
+  dev::Prep pr;
+  pr.n = n;
+  pr.C = C;
+  pr.L = L;
+  pr.icb = b->inst_clause_begin;
+  pr.cb = b->clause_begin;
+  pr.lits = b->lits;
+  pr.nv = b->inst_num_vars;
+  pr.occ_base = static_cast<int64_t*>(at(o_occ_base));
+  pr.norm = static_cast<uint32_t*>(at(o_norm));
+  pr.occ_cnt = static_cast<uint32_t*>(at(o_occ_cnt));
+  pr.occ_begin = static_cast<uint32_t*>(at(o_occ_begin));
+  pr.ent = static_cast<uint64_t*>(at(o_ent));
+  pr.units = static_cast<uint32_t*>(at(o_units));
+  pr.nunits = static_cast<uint32_t*>(at(o_nunits));
+  pr.flags = static_cast<uint32_t*>(at(o_flags));
+  pr.total_vars = b->total_vars;
+  pr.occ_cap = occ_total;
+  pr.vmax = vmax;
+  pr.vb = b->inst_var_begin;
+  pr.ctrl = static_cast<dev::Ctrl*>(at(o_ctrl));
+
+  // the array keeps the previous call's contents: everything that must start
+  // at zero is cleared here, the rest is written before it is read
+  dev::k_init_ctrl<<<1, 1, 0, st>>>(pr.ctrl, (uint32_t)n);
+  cudaMemsetAsync(pr.occ_cnt, 0, 4 * (size_t)occ_total, st);
+  cudaMemsetAsync(pr.flags, 0, 4 * (size_t)n, st);
+  dev::k_occ_base<<<1, 1024, 0, st>>>(pr);
+  if (C > 0) {
+    int grid = (int)std::min<int64_t>((C + 255) / 256, (int64_t)sms * 32);
+    dev::k_normalize<<<grid, 256, 0, st>>>(pr);
+  }
+  int wgrid = (int)std::min<int64_t>((n + 7) / 8, (int64_t)sms * 16);
+  dev::k_occ_scan<<<wgrid, 256, 0, st>>>(pr);
+  dev::k_fill<<<wgrid, 256, 0, st>>>(pr);
+
+  dev::Solve sv;
+  std::memset(&sv, 0, sizeof(sv));
+  sv.n = n;
+  sv.vmax = vmax;
+  sv.assign_words = assign_words;
+  sv.icb = b->inst_clause_begin;
+  sv.cb = b->clause_begin;
+  sv.lits = b->lits;
+  sv.nv = b->inst_num_vars;
+  sv.vb = b->inst_var_begin;
+  sv.occ_base = pr.occ_base;
+  sv.occ_begin = pr.occ_begin;
+  sv.ent = pr.ent;
+  sv.units = pr.units;
+  sv.nunits = pr.nunits;
+  sv.flags = pr.flags;
+  sv.order = opt->order;
+  sv.verdict = verdict;
+  sv.model = model;
+  sv.stats = opt->stats;
+  sv.pending = static_cast<uint32_t*>(at(o_pending));
+  sv.done = static_cast<uint32_t*>(at(o_done));
+  sv.inst_dec = static_cast<unsigned long long*>(at(o_inst_dec));
+  sv.trail = static_cast<uint32_t*>(at(o_trail));
+  sv.dstack = static_cast<uint32_t*>(at(o_dstack));
+  sv.act = static_cast<float*>(at(o_act));
+  sv.ring = static_cast<dev::Job*>(at(o_ring));
+  sv.ring_cap = ring_cap;
+  sv.job_act = static_cast<float*>(at(o_job_act));
+  sv.prefix = static_cast<uint32_t*>(at(o_prefix));
+  sv.split_min = opt->split_min > 0 ? opt->split_min : 256;
+  sv.ctrl = pr.ctrl;
+  sv.budget = opt->decision_budget;
+  int64_t tb = opt->time_budget_ms > 0 ? opt->time_budget_ms : 600000;
+  sv.time_ns = (uint64_t)tb * 1000000ull;
+  sv.abort_flag = opt->abort_flag;
+  sv.split = opt->split ? 1 : 0;
+  sv.split_interval = opt->split_interval > 0 ? opt->split_interval : 16;
+  sv.trail_smem = 0;
+  sv.finish_ns = nullptr;
+  sv.prof = nullptr;
+
+  dev::k_init_ring<<<4, 256, 0, st>>>(sv.ring, ring_cap);
+  dev::k_init_inst<<<(n + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec, n);
+  dev::k_start_clock<<<1, 1, 0, st>>>(sv.ctrl);
+  e = cudaFuncSetAttribute(dev::k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
+  dev::k_solve<<<sms, 32 * wpb, smem, st>>>(sv);
+  dev::k_finalize<<<(n + 255) / 256, 256, 0, st>>>(sv);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("kernel launch", e);
+  // report the device-side status of this call (the control block lives in
+  // the static array, so the normal status query cannot see it)
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("cudaStreamSynchronize", e);
+  int32_t status = 0;
+  e = cudaMemcpy(&status, reinterpret_cast<unsigned char*>(pr.ctrl) + offsetof(dev::Ctrl, status),
+                 sizeof(status), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail("cudaMemcpy", e);
+  if (status != 0) set_error("scuba_solve_batch_noalloc: device status " + std::to_string(status));
+  return status;
 }
