@@ -82,6 +82,34 @@ typedef struct scuba_cnf_batch {
   const int64_t* inst_var_begin;
 } scuba_cnf_batch;
 
+/*
+ * Decision traces of the plain search, the training data of the branching
+ * network (not in the paper; its solver is CP-SAT, Sec. V-B). With
+ * scuba_options.trace set, the search runs one warp per instance (no subtree
+ * sharing) with activity branching and records every decision at depth <
+ * `depth` as a node: the features of every variable unassigned at that point
+ * (rows x[r*16 .. r*16+15], BF16, layout of scuba_mlp_layout) and, once the
+ * node's subtree is finished, target[r] = how many falsified clauses of that
+ * subtree contained variable var[r]. All arrays are DEVICE memory owned by
+ * the caller; counts[0]/counts[1] (zero them before the call) return the
+ * nodes and rows reserved -- recording stops when a capacity is reached.
+ * node_closed[k] = 1 once node k's subtree is complete.
+ */
+typedef struct scuba_trace {
+  int32_t depth;         /* 1..8 */
+  int64_t max_nodes;
+  int64_t max_rows;
+  int64_t* counts;       /* [2] */
+  int32_t* node_inst;    /* [max_nodes] instance of the node */
+  int32_t* node_depth;   /* [max_nodes] decision depth */
+  int64_t* node_row;     /* [max_nodes] first row */
+  int32_t* node_nrows;   /* [max_nodes] rows (unassigned variables) */
+  int32_t* node_closed;  /* [max_nodes] */
+  uint16_t* x;           /* [max_rows*16] features, BF16 bits */
+  float* target;         /* [max_rows] */
+  int32_t* var;          /* [max_rows] variable index (0-based) */
+} scuba_trace;
+
 /* Options for scuba_solve_batch_ex. Initialise with scuba_options_init(). */
 typedef struct scuba_options {
   int32_t heuristic;         /* SCUBA_HEUR_ACTIVITY or SCUBA_HEUR_LEARNED */
@@ -113,6 +141,10 @@ typedef struct scuba_options {
   void* search_event_begin;  /* cudaEvent_t recorded on `stream` right before the
                                 search kernel launch; may be NULL */
   void* search_event_end;    /* cudaEvent_t recorded right after it; may be NULL */
+  const int32_t* inst_num_inputs; /* device [num_instances] or NULL: number of input
+                                     bits of each query (the encoder numbers them
+                                     first); a feature of the branching network */
+  const scuba_trace* trace;  /* host struct of device buffers, or NULL */
 } scuba_options;
 
 /* Number of int64 counters per instance in scuba_options.stats. */
@@ -237,6 +269,64 @@ void scuba_encoded_free(scuba_encoded* enc);
 int scuba_verify_batch(const scuba_encoded* enc, const int64_t* irs, const int64_t* ir_offsets,
                        const uint8_t* verdict, const uint8_t* model, int32_t nthreads,
                        uint8_t* ok);
+
+/* ------------------------------------------------------------------------- */
+/* Learned branching: the incidence MLP (not in the paper)                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The network scores a variable from 16 features of the residual formula:
+ * score = w2 . relu(W1 x + b1) + b2, 16 -> 64 -> 1. Packed device weights
+ * (the layout the solver reads; BF16 matrices, FP32 biases):
+ *   bytes [0, 2048)      W1 transposed, bf16 w1t[64][16] (w1t[j][i] = W1[i][j])
+ *   bytes [2048, 2176)   w2, bf16 [64]
+ *   bytes [2176, 2432)   b1, fp32 [64]
+ *   bytes [2432, 2436)   b2, fp32; then 12 bytes of padding (2448 bytes)
+ * FP32 master parameters (NPARAM = 1153): W1[i][j] at i*64 + j, b1 at 1024,
+ * w2 at 1088, b2 at 1152.
+ * Features per row (x[r*16 + k], BF16): for the positive then the negative
+ * literal, unsatisfied clauses holding it with 2 and with 3 open literals
+ * (x0..x3, /4), static occurrences (x4, x5, /8), activity/increment (x6),
+ * input-bit flag and position (x7, x8), depth/32 (x9), assigned fraction
+ * (x10), binary and ternary totals (x11, x12, /8), log2 occurrences (x13),
+ * polarity balance (x14), constant 1 (x15).
+ */
+#define SCUBA_MLP_WEIGHT_BYTES 2448
+#define SCUBA_MLP_NPARAM 1153
+
+/* out[4] = {weight bytes, NPARAM, features, hidden units}. */
+int scuba_mlp_layout(int64_t* out);
+
+/* He-initialise the FP32 master parameters from `seed` and pack them into
+   the device weights. Both pointers are device memory. Asynchronous. */
+int scuba_mlp_init(float* master, void* weights, uint64_t seed, void* stream);
+
+/* Pack FP32 master parameters into the BF16 device weights. Asynchronous. */
+int scuba_mlp_pack(const float* master, void* weights, void* stream);
+
+/* scores[r] for rows [0, rows) of x (device, BF16 [rows][16]), on the tensor
+   cores (BF16 inputs, FP32 accumulation). Asynchronous. */
+int scuba_mlp_forward(const uint16_t* x, int64_t rows, const void* weights, float* scores,
+                      void* stream);
+
+/* Gradient of the summed node losses over trace nodes [node_begin,
+   node_end): per node, cross-entropy between the normalised targets and the
+   softmax of its rows' scores (nodes not closed, with one row, or with zero
+   targets are skipped). grad: device float[NPARAM + 2], overwritten; the
+   last two entries are the summed loss and the nodes used. dS: device
+   float[trace->max_rows] scratch (receives dLoss/dscore). Asynchronous. */
+int scuba_mlp_grad(const scuba_trace* trace, int64_t node_begin, int64_t node_end,
+                   const void* weights, float* grad, float* dS, void* stream);
+
+/* Adam training (lr, beta 0.9/0.999, mean loss over the nodes of each
+   minibatch of `batch_nodes` consecutive nodes) for `epochs` passes over
+   trace nodes [0, nodes). master, adam_m, adam_v: device float[NPARAM]
+   (the moments are reset); weights: device packed weights, kept in sync.
+   epoch_loss: device float[2*epochs] or NULL: summed loss and nodes used per
+   epoch. Asynchronous (allocates its scratch on first use). */
+int scuba_mlp_train(const scuba_trace* trace, int64_t nodes, float* master, float* adam_m,
+                    float* adam_v, void* weights, int32_t epochs, int32_t batch_nodes, float lr,
+                    float* epoch_loss, void* stream);
 
 #ifdef __cplusplus
 }

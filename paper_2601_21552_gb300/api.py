@@ -6,6 +6,8 @@ the ``scuba_cnf_batch`` / ``scuba_options`` structs and call the ABI.
 """
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 import torch
 
@@ -38,11 +40,48 @@ class DeviceBatch:
         self.h2d_bytes = sum(int(x.nbytes) for x in (enc.inst_clause_begin, enc.clause_begin,
                                                        enc.lits, enc.inst_num_vars,
                                                        enc.inst_var_begin))
+        # input bits per instance (the encoder numbers them first): a feature
+        # of the branching network
+        iib, widths, _ = enc.inputs()
+        csum = np.concatenate([[0], np.cumsum(widths, dtype=np.int64)])
+        ninp = (csum[iib[1:]] - csum[iib[:-1]]).astype(np.int32) if self.n else np.zeros(1, np.int32)
+        self.num_inputs = up(ninp if self.n else np.zeros(1, np.int32))
 
     def struct(self) -> B.scuba_cnf_batch:
         return B.make_batch(self.n, self.max_vars, self.total_clauses, self.total_lits,
                             self.total_vars, self.icb.data_ptr(), self.cb.data_ptr(),
                             self.lits.data_ptr(), self.nv.data_ptr(), self.vb.data_ptr())
+
+
+class Trace:
+    """Device buffers of a decision trace (scuba_trace), torch-owned."""
+
+    def __init__(self, depth: int, max_nodes: int, max_rows: int, device="cuda"):
+        dev = torch.device(device)
+        z = lambda n, dt: torch.zeros(max(n, 1), dtype=dt, device=dev)
+        self.depth, self.max_nodes, self.max_rows = depth, max_nodes, max_rows
+        self.counts = z(2, torch.int64)
+        self.node_inst = z(max_nodes, torch.int32)
+        self.node_depth = z(max_nodes, torch.int32)
+        self.node_row = z(max_nodes, torch.int64)
+        self.node_nrows = z(max_nodes, torch.int32)
+        self.node_closed = z(max_nodes, torch.int32)
+        self.x = z(max_rows * 16, torch.int16)
+        self.target = z(max_rows, torch.float32)
+        self.var = z(max_rows, torch.int32)
+
+    def struct(self) -> B.scuba_trace:
+        t = B.scuba_trace()
+        t.depth, t.max_nodes, t.max_rows = self.depth, self.max_nodes, self.max_rows
+        for name in ("counts", "node_inst", "node_depth", "node_row", "node_nrows",
+                     "node_closed", "x", "target", "var"):
+            setattr(t, name, getattr(self, name).data_ptr())
+        return t
+
+    def used(self) -> tuple[int, int]:
+        """(nodes, rows) actually recorded (capped at the capacities)."""
+        c = self.counts.cpu().tolist()
+        return min(c[0], self.max_nodes), min(c[1], self.max_rows)
 
 
 def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
@@ -51,7 +90,8 @@ def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
             order: torch.Tensor | None = None, mlp_weights: torch.Tensor | None = None,
             learned_depth: int = 0, abort_flag_ptr: int | None = None,
             events: tuple | None = None, finish_ns: torch.Tensor | None = None,
-            profile: torch.Tensor | None = None) -> B.scuba_options:
+            profile: torch.Tensor | None = None, num_inputs: torch.Tensor | None = None,
+            trace: "Trace | None" = None) -> B.scuba_options:
     o = B.scuba_options_init()
     o.heuristic = heuristic
     o.decision_budget = decision_budget
@@ -67,6 +107,10 @@ def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
     o.mlp_weights = mlp_weights.data_ptr() if mlp_weights is not None else None
     o.learned_depth = learned_depth
     o.abort_flag = abort_flag_ptr
+    o.inst_num_inputs = num_inputs.data_ptr() if num_inputs is not None else None
+    if trace is not None:
+        o._trace_keep = trace.struct()          # keep the struct alive with the options
+        o.trace = ctypes.addressof(o._trace_keep)
     o.finish_ns = finish_ns.data_ptr() if finish_ns is not None else None
     o.profile = profile.data_ptr() if profile is not None else None
     if events is not None:
@@ -85,6 +129,7 @@ def solve(db: DeviceBatch, want_model: bool = True, stats: bool = True,
     verdict = torch.empty(max(db.n, 1), dtype=torch.uint8, device=dev)
     model = torch.zeros(max(db.total_vars, 1), dtype=torch.uint8, device=dev) if want_model else None
     st = torch.zeros((max(db.n, 1), B.SCUBA_NSTATS), dtype=torch.int64, device=dev) if stats else None
+    opts.setdefault("num_inputs", db.num_inputs)
     o = options(stats=st, **opts)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     B.scuba_solve_batch_ex(db.struct(), verdict.data_ptr(),
@@ -111,3 +156,45 @@ def solve_queries(irs: list, device: str = "cuda", **opts):
     fails, ok = B.scuba_verify_batch(enc, vh, mh)
     return dict(verdict=vh, stats=st.cpu().numpy() if st is not None else None,
                 verified=ok, fails=fails, status=rc, enc=enc, model=mh)
+
+
+class Mlp:
+    """The branching network: FP32 master parameters, Adam moments and the
+    packed BF16 weights the solver reads, all device tensors."""
+
+    def __init__(self, seed: int = 1, device="cuda"):
+        dev = torch.device(device)
+        self.master = torch.zeros(B.SCUBA_MLP_NPARAM, dtype=torch.float32, device=dev)
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        self.weights = torch.zeros(B.SCUBA_MLP_WEIGHT_BYTES, dtype=torch.uint8, device=dev)
+        s = torch.cuda.current_stream(dev).cuda_stream
+        B._check(B._lib.scuba_mlp_init(self.master.data_ptr(), self.weights.data_ptr(),
+                                       ctypes.c_uint64(seed), s), "scuba_mlp_init")
+
+    def train(self, trace: Trace, epochs: int = 10, batch_nodes: int = 64, lr: float = 3e-3):
+        """Adam over the recorded nodes; returns the mean loss per epoch."""
+        nodes, _ = trace.used()
+        loss = torch.zeros(2 * max(epochs, 1), dtype=torch.float32, device=self.master.device)
+        t = trace.struct()
+        s = torch.cuda.current_stream(self.master.device).cuda_stream
+        B._check(B._lib.scuba_mlp_train(ctypes.byref(t), nodes, self.master.data_ptr(),
+                                        self.m.data_ptr(), self.v.data_ptr(),
+                                        self.weights.data_ptr(), epochs, batch_nodes,
+                                        ctypes.c_float(lr), loss.data_ptr(), s),
+                 "scuba_mlp_train")
+        lh = loss.cpu().numpy().reshape(-1, 2)[:epochs]
+        return (lh[:, 0] / np.maximum(lh[:, 1], 1)).tolist()
+
+
+def record_trace(db: DeviceBatch, depth: int = 6, max_nodes: int = 1 << 16,
+                 max_rows: int = 1 << 24, decision_budget: int = 0, time_budget_ms: int = 0):
+    """Run the plain search in trace mode (one warp per instance) and return
+    (Trace, verdict, stats)."""
+    tr = Trace(depth, max_nodes, max_rows, db.icb.device)
+    v, _, st = solve(db, want_model=False, trace=tr, decision_budget=decision_budget,
+                     time_budget_ms=time_budget_ms, split=False)
+    rc = status()
+    if rc != 0:
+        raise RuntimeError(f"trace solve failed with status {rc}")
+    return tr, v, st

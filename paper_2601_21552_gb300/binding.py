@@ -46,7 +46,15 @@ class scuba_options(ctypes.Structure):
                 ("split_min", _i32), ("trail_placement", _i32), ("finish_ns", _vp),
                 ("profile", _vp),
                 ("stats", _vp), ("order", _vp), ("abort_flag", _vp),
-                ("search_event_begin", _vp), ("search_event_end", _vp)]
+                ("search_event_begin", _vp), ("search_event_end", _vp),
+                ("inst_num_inputs", _vp), ("trace", _vp)]
+
+
+class scuba_trace(ctypes.Structure):
+    _fields_ = [("depth", _i32), ("max_nodes", _i64), ("max_rows", _i64), ("counts", _vp),
+                ("node_inst", _vp), ("node_depth", _vp), ("node_row", _vp),
+                ("node_nrows", _vp), ("node_closed", _vp), ("x", _vp), ("target", _vp),
+                ("var", _vp)]
 
 
 SCUBA_NSTATS = 6
@@ -79,13 +87,24 @@ _sig("scuba_encoded_copy", _i32, [_vp, _vp, _vp, _vp, _vp, _vp])
 _sig("scuba_encoded_inputs", _i32, [_vp, _vp, _vp, _vp])
 _sig("scuba_encoded_free", None, [_vp])
 _sig("scuba_verify_batch", _i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp])
+_sig("scuba_mlp_layout", _i32, [_vp])
+_sig("scuba_mlp_init", _i32, [_vp, _vp, ctypes.c_uint64, _vp])
+_sig("scuba_mlp_pack", _i32, [_vp, _vp, _vp])
+_sig("scuba_mlp_forward", _i32, [_vp, _i64, _vp, _vp, _vp])
+_sig("scuba_mlp_grad", _i32, [ctypes.POINTER(scuba_trace), _i64, _i64, _vp, _vp, _vp, _vp])
+_sig("scuba_mlp_train", _i32, [ctypes.POINTER(scuba_trace), _i64, _vp, _vp, _vp, _vp, _i32,
+                               _i32, ctypes.c_float, _vp, _vp])
 
 EXPORTED = [
     "scuba_options_init", "scuba_solve_batch", "scuba_solve_batch_ex",
     "scuba_solve_batch_host", "scuba_solve_batch_noalloc", "scuba_sync_status", "scuba_release", "scuba_last_error",
     "scuba_version", "scuba_abi_sizes", "scuba_encode_batch", "scuba_encoded_sizes", "scuba_encoded_copy",
     "scuba_encoded_inputs", "scuba_encoded_free", "scuba_verify_batch",
+    "scuba_mlp_layout", "scuba_mlp_init", "scuba_mlp_pack", "scuba_mlp_forward",
+    "scuba_mlp_grad", "scuba_mlp_train",
 ]
+SCUBA_MLP_WEIGHT_BYTES = 2448
+SCUBA_MLP_NPARAM = 1153
 
 
 def _np_ptr(a: np.ndarray):

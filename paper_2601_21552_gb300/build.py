@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libscuba.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 HOST_SRCS = ["encoder.cpp", "verify.cpp", "host_api.cpp"]
-CUDA_SRCS = ["solver.cu"]
+CUDA_SRCS = ["solver.cu", "mlp.cu"]
 
 
 def _nvcc() -> str:

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "../../include/scuba.h"
+#include "learn.cuh"
 #include "scuba_internal.h"
 
 namespace scuba {
@@ -332,6 +333,22 @@ struct Job {            // a DPLL subtree: the instance plus assumed literals
   float inc;            // donor's activity increment; its activities are in job_act
 };
 
+// Decision-trace buffers (training data for the branching network).
+struct TraceDev {
+  unsigned long long* cursor;  // [2]: nodes, rows reserved
+  int64_t max_nodes, max_rows;
+  int32_t* node_inst;
+  int32_t* node_depth;
+  int64_t* node_row;
+  int32_t* node_nrows;
+  int32_t* node_closed;
+  __nv_bfloat16* x;            // [max_rows][NFEAT]
+  float* target;               // [max_rows]
+  int32_t* var;                // [max_rows]
+};
+
+enum { MODE_PLAIN = 0, MODE_TRACE = 1, MODE_LEARNED = 2 };
+
 struct Solve {
   int n;
   int32_t vmax;
@@ -374,6 +391,14 @@ struct Solve {
   int trail_smem;          // 1: each warp's trail lives in shared memory
   int64_t* finish_ns;      // optional [n]: completion time of each instance
   unsigned long long* prof;  // optional [8]: search counters
+  // learned branching and trace recording
+  const learn::MlpWeights* mlp;
+  int learned_depth;           // MLP decides at decision depth < learned_depth
+  const int32_t* inst_num_inputs;  // optional [n]: input bits (numbered first)
+  int trace_depth;             // record decisions at depth < trace_depth
+  TraceDev tr;
+  uint32_t* lvlcnt;            // [slots][MAX_TRACE_DEPTH][vmax] conflict counts
+  int64_t* lvl_node;           // [slots][MAX_TRACE_DEPTH] node of each open level
 };
 
 struct WarpShared {
@@ -414,6 +439,9 @@ struct Warp {
   uint32_t nd_fixed;       // decisions below this index are assumptions
   float inc;
   uint32_t decisions;      // decisions of the current job
+  uint32_t* lvlcnt;        // trace: per-level conflict counts of this slot
+  int64_t* lvl_node;       // trace: node of each open level
+  __nv_bfloat16* xtile;    // learned: 32 x NFEAT feature tile in shared memory
 };
 
 #define WCOUNT(w, field, amount)                 \
@@ -570,9 +598,26 @@ __device__ bool bcp(Warp& w) {
   }
 }
 
+template <int MODE>
 __device__ void bump(Warp& w) {
   // activity += inc for the variables of the falsified clause
   const uint32_t a = w.ws->cl[0], b = w.ws->cl[1], c = w.ws->cl[2];
+  if (MODE == MODE_TRACE) {
+    // every open traced level counts the falsified clause's variables
+    const uint32_t levels = min(w.nd, (uint32_t)w.S->trace_depth);
+    if ((uint32_t)w.lane < levels) {
+      uint32_t* cnt = w.lvlcnt + (size_t)w.lane * w.S->vmax;
+      if (a & LONG_CLAUSE) {
+        const int64_t cl = w.c0 + (a & ~LONG_CLAUSE);
+        for (int64_t q = w.S->cb[cl]; q < w.S->cb[cl + 1]; q++) cnt[code_of(w.S->lits[q]) >> 1]++;
+      } else {
+        if (a != NONE) cnt[a >> 1]++;
+        if (b != NONE) cnt[b >> 1]++;
+        if (c != NONE) cnt[c >> 1]++;
+      }
+    }
+    __syncwarp();
+  }
   bool big = false;
   if (w.lane == 0) {
     if (a & LONG_CLAUSE) {
@@ -602,8 +647,174 @@ __device__ void bump(Warp& w) {
   }
 }
 
+// ---- features of the residual formula (learned branching, traces) -------
+//
+// For variable v (0-based) and each polarity: how many clauses containing the
+// literal are not yet satisfied with 2 / 3 open literals, its static
+// occurrence count, plus activity, input-bit flags and search progress.
+__device__ void var_features(const Warp& w, uint32_t v, uint32_t ninputs, float f[16]) {
+  uint32_t c2[2] = {0, 0}, c3[2] = {0, 0}, occn[2];
+#pragma unroll
+  for (int pol = 0; pol < 2; pol++) {
+    const uint32_t lit = 2u * v + (uint32_t)pol;
+    const uint32_t beg = __ldg(&w.occ[lit]), end = __ldg(&w.occ[lit + 1]);
+    occn[pol] = end - beg;
+    for (uint32_t e = beg; e < end; e++) {
+      const uint64_t en = __ldg(&w.ent[e]);
+      const uint32_t a = (uint32_t)en, b = (uint32_t)(en >> 32);
+      if (a & LONG_CLAUSE) continue;
+      const uint32_t va = lit_value(w.asg, a);
+      if (va == LV_T || va == LV_X) continue;
+      uint32_t open = 1 + (va == LV_U);
+      if (b != NONE) {
+        const uint32_t vb = lit_value(w.asg, b);
+        if (vb == LV_T || vb == LV_X) continue;
+        open += (vb == LV_U);
+      }
+      if (open == 2) c2[pol]++;
+      else if (open == 3) c3[pol]++;
+    }
+  }
+  const float tail = (float)*(volatile uint32_t*)&w.ws->tail;
+  f[0] = c2[0] * 0.25f;
+  f[1] = c3[0] * 0.25f;
+  f[2] = c2[1] * 0.25f;
+  f[3] = c3[1] * 0.25f;
+  f[4] = occn[0] * 0.125f;
+  f[5] = occn[1] * 0.125f;
+  f[6] = fminf(w.act[v] / w.inc, 16.0f) * 0.0625f;
+  f[7] = v < ninputs ? 1.0f : 0.0f;
+  f[8] = v < ninputs ? (float)v / (float)ninputs : 0.0f;
+  f[9] = (float)w.nd * (1.0f / 32.0f);
+  f[10] = w.V ? tail / (float)w.V : 0.0f;
+  f[11] = (c2[0] + c2[1]) * 0.125f;
+  f[12] = (c3[0] + c3[1]) * 0.125f;
+  f[13] = log2f(1.0f + occn[0] + occn[1]) * (1.0f / 6.0f);
+  f[14] = ((float)(c2[0] + c3[0]) - (float)(c2[1] + c3[1])) * 0.125f;
+  f[15] = 1.0f;
+}
+
+__device__ __forceinline__ bool var_unassigned(const uint32_t* asg, uint32_t v) {
+  return ((asg[v >> 4] >> ((v & 15u) * 2u)) & 3u) == 0u;
+}
+
+// Trace: open a node for the decision about to be made at level `depth`.
+__device__ void trace_open(Warp& w, uint32_t depth) {
+  const Solve& S = *w.S;
+  const TraceDev& T = S.tr;
+  uint32_t nun = 0;
+  for (uint32_t base = 0; base < w.V; base += 32) {
+    const uint32_t v = base + w.lane;
+    nun += __popc(__ballot_sync(FULL, v < w.V && var_unassigned(w.asg, v)));
+  }
+  long long node = -1, row0 = 0;
+  if (w.lane == 0) {
+    node = (long long)atomicAdd(&T.cursor[0], 1ull);
+    row0 = (long long)atomicAdd(&T.cursor[1], (unsigned long long)nun);
+    if (node >= T.max_nodes || row0 + nun > T.max_rows) node = -1;
+  }
+  node = __shfl_sync(FULL, node, 0);
+  row0 = __shfl_sync(FULL, row0, 0);
+  if (w.lane == 0) w.lvl_node[depth] = node;
+  if (node < 0) return;
+  if (w.lane == 0) {
+    T.node_inst[node] = w.inst;
+    T.node_depth[node] = (int32_t)depth;
+    T.node_row[node] = row0;
+    T.node_nrows[node] = (int32_t)nun;
+    T.node_closed[node] = 0;
+  }
+  const uint32_t ni = S.inst_num_inputs ? (uint32_t)S.inst_num_inputs[w.inst] : 0u;
+  long long r = row0;
+  for (uint32_t base = 0; base < w.V; base += 32) {
+    const uint32_t v = base + w.lane;
+    const bool un = v < w.V && var_unassigned(w.asg, v);
+    const uint32_t m = __ballot_sync(FULL, un);
+    if (un) {
+      const long long row = r + __popc(m & ((1u << w.lane) - 1u));
+      float f[16];
+      var_features(w, v, ni, f);
+      __nv_bfloat16* xr = T.x + row * learn::NFEAT;
+#pragma unroll
+      for (int k = 0; k < 16; k++) xr[k] = __float2bfloat16(f[k]);
+      T.var[row] = (int32_t)v;
+      T.target[row] = 0.0f;
+    }
+    r += __popc(m);
+  }
+  __syncwarp();
+}
+
+// Trace: the subtree of level l is finished; write its conflict counts.
+__device__ void trace_close(Warp& w, uint32_t l) {
+  const TraceDev& T = w.S->tr;
+  const long long node = w.lvl_node[l];
+  uint32_t* cnt = w.lvlcnt + (size_t)l * w.S->vmax;
+  if (node >= 0) {
+    const long long row0 = T.node_row[node];
+    const int32_t nr = T.node_nrows[node];
+    for (int k = w.lane; k < nr; k += 32) T.target[row0 + k] = (float)cnt[T.var[row0 + k]];
+    __syncwarp();
+    if (w.lane == 0) T.node_closed[node] = 1;
+  }
+  for (uint32_t v = w.lane; v < w.V; v += 32) cnt[v] = 0u;
+  __syncwarp();
+  if (w.lane == 0) w.lvl_node[l] = -1;
+  __syncwarp();
+}
+
+// Learned decision: the unassigned variable with the highest MLP score
+// (ties: higher activity, then lower id). NONE if all are assigned.
+__device__ uint32_t pick_learned(Warp& w) {
+  const Solve& S = *w.S;
+  const uint32_t ni = S.inst_num_inputs ? (uint32_t)S.inst_num_inputs[w.inst] : 0u;
+  float best_s = -INFINITY, best_a = -1.0f;
+  uint32_t best_v = NONE;
+  for (uint32_t base = 0; base < w.V; base += 32) {
+    const uint32_t v = base + w.lane;
+    const bool un = v < w.V && var_unassigned(w.asg, v);
+    if (!__any_sync(FULL, un)) continue;
+    float f[16];
+    if (un) var_features(w, v, ni, f);
+    else
+      for (int k = 0; k < 16; k++) f[k] = 0.0f;
+    __nv_bfloat16* xr = w.xtile + w.lane * learn::NFEAT;
+#pragma unroll
+    for (int k = 0; k < 16; k++) xr[k] = __float2bfloat16(f[k]);
+    __syncwarp();
+    float a_lo, a_hi, b_lo, b_hi;
+    learn::mlp_tile_scores(S.mlp, w.xtile, w.lane, a_lo, a_hi);
+    learn::mlp_tile_scores(S.mlp, w.xtile + 16 * learn::NFEAT, w.lane, b_lo, b_hi);
+    // lane 4g holds rows g, g+8 (first tile) and 16+g, 24+g (second tile)
+    const int src = 4 * (w.lane & 7);
+    const float r0 = __shfl_sync(FULL, a_lo, src), r1 = __shfl_sync(FULL, a_hi, src);
+    const float r2 = __shfl_sync(FULL, b_lo, src), r3 = __shfl_sync(FULL, b_hi, src);
+    const float sc = w.lane < 8 ? r0 : (w.lane < 16 ? r1 : (w.lane < 24 ? r2 : r3));
+    if (un) {
+      const float a = w.act[v];
+      if (sc > best_s || (sc == best_s && (a > best_a || (a == best_a && v < best_v)))) {
+        best_s = sc;
+        best_a = a;
+        best_v = v;
+      }
+    }
+    __syncwarp();
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    const float os = __shfl_xor_sync(FULL, best_s, d), oa = __shfl_xor_sync(FULL, best_a, d);
+    const uint32_t ov = __shfl_xor_sync(FULL, best_v, d);
+    if (os > best_s || (os == best_s && (oa > best_a || (oa == best_a && ov < best_v)))) {
+      best_s = os;
+      best_a = oa;
+      best_v = ov;
+    }
+  }
+  return best_v;
+}
+
 // Chronological backtrack after a conflict. Returns false when no decision
 // above the assumptions is left to flip (the subtree is refuted).
+template <int MODE>
 __device__ bool backtrack(Warp& w) {
   uint32_t nd = w.nd;
   if (w.lane == 0)
@@ -611,6 +822,11 @@ __device__ bool backtrack(Warp& w) {
   nd = __shfl_sync(FULL, nd, 0);
   __syncwarp();
   if (nd <= w.nd_fixed) return false;
+  if (MODE == MODE_TRACE) {
+    // levels nd .. w.nd-1 are popped: their subtrees are complete
+    const uint32_t hi_l = min(w.nd, (uint32_t)w.S->trace_depth);
+    for (uint32_t l = nd; l < hi_l; l++) trace_close(w, l);
+  }
   const uint32_t pos = w.dstack[nd - 1] & ~FLIP;
   const uint32_t tail = *(volatile uint32_t*)&w.ws->tail;
   const uint32_t d = w.trail[pos];
@@ -787,7 +1003,24 @@ struct TakenJob {
   float inc;            // activities were copied into the warp's act[] already
 };
 
+template <int MODE>
+__device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* job,
+                            int& abort_code);
+
+// Runs one job; in trace mode every level still open at the end is closed.
+template <int MODE>
 __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, int& abort_code) {
+  const int r = run_job_body<MODE>(S, w, inst, job, abort_code);
+  if (MODE == MODE_TRACE) {
+    const uint32_t hi_l = min(w.nd, (uint32_t)S.trace_depth);
+    for (uint32_t l = 0; l < hi_l; l++) trace_close(w, l);
+  }
+  return r;
+}
+
+template <int MODE>
+__device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* job,
+                            int& abort_code) {
   w.inst = inst;
   w.V = (uint32_t)S.nv[inst];
   w.c0 = S.icb[inst];
@@ -850,12 +1083,15 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, i
     }
     if (bcp(w)) {
       WCOUNT(w, conflicts, 1);
-      bump(w);
-      if (!backtrack(w)) return SCUBA_UNSAT;
+      bump<MODE>(w);
+      if (!backtrack<MODE>(w)) return SCUBA_UNSAT;
       continue;
     }
     WCOUNT(w, act_reads, w.V - *(volatile uint32_t*)&w.ws->tail);
-    const uint32_t v = pick(w);
+    uint32_t v;
+    if (MODE == MODE_LEARNED && w.nd < (uint32_t)S.learned_depth) v = pick_learned(w);
+    else v = pick(w);
+    if (MODE == MODE_TRACE && v != NONE && w.nd < (uint32_t)S.trace_depth) trace_open(w, w.nd);
     if (v == NONE) {
       // the first subtree of the instance to reach a model writes it
       uint32_t won = 0;
@@ -919,8 +1155,11 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, i
   }
 }
 
-// 48 registers per thread: 5 blocks x 8 warps = 40 resident warps per SM
-__global__ void __launch_bounds__(256, 5) k_solve(const __grid_constant__ Solve S) {
+// Plain search: 48 registers per thread, 5 blocks x 8 warps = 40 resident
+// warps per SM. The learned variant (MLP on the tensor cores) gets 64.
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? 4 : 5)
+    k_solve(const __grid_constant__ Solve S) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -938,6 +1177,20 @@ __global__ void __launch_bounds__(256, 5) k_solve(const __grid_constant__ Solve 
   w.dstack = S.dstack + slot * S.vmax;
   w.act = S.act + slot * S.vmax;
   w.lane = lane;
+  w.lvlcnt = nullptr;
+  w.lvl_node = nullptr;
+  w.xtile = nullptr;
+  if (MODE == MODE_TRACE) {
+    w.lvlcnt = S.lvlcnt + (size_t)slot * learn::MAX_TRACE_DEPTH * S.vmax;
+    w.lvl_node = S.lvl_node + (size_t)slot * learn::MAX_TRACE_DEPTH;
+  }
+  if (MODE == MODE_LEARNED) {
+    // feature tile after the per-warp assignment (and trail) areas
+    unsigned char* tiles = reinterpret_cast<unsigned char*>(
+        smem + (sizeof(WarpShared) / 4) * wpb + (size_t)S.assign_words * wpb +
+        (S.trail_smem ? (size_t)S.vmax * wpb : 0));
+    w.xtile = reinterpret_cast<__nv_bfloat16*>(tiles) + (size_t)wib * 32 * learn::NFEAT;
+  }
   if (batch_failed(S.ctrl)) return;
   bool counted_idle = false;
   for (;;) {
@@ -1013,7 +1266,7 @@ __global__ void __launch_bounds__(256, 5) k_solve(const __grid_constant__ Solve 
     } else if (moot) {
       r = SCUBA_UNSAT;  // moot: another subtree already found a model
     } else {
-      r = run_job(S, w, inst, job, abort_code);
+      r = run_job<MODE>(S, w, inst, job, abort_code);
     }
     finish_job(S, w, inst, r);
     if (abort_code) {
@@ -1074,6 +1327,7 @@ struct Buf {
 struct Scratch {
   Buf occ_base, norm, occ_cnt, occ_begin, ent, units, nunits, flags;
   Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
+  Buf lvlcnt, lvl_node;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
   int32_t last_status = 0;
@@ -1165,6 +1419,23 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
     set_error("scuba_solve_batch: instance too large");
     return SCUBA_ERR_TOO_LARGE;
   }
+  int mode = dev::MODE_PLAIN;
+  if (opt->trace) {
+    const scuba_trace* T = opt->trace;
+    if (T->depth < 1 || T->depth > learn::MAX_TRACE_DEPTH || T->max_nodes < 0 ||
+        T->max_rows < 0 || !T->counts || !T->node_inst || !T->node_depth || !T->node_row ||
+        !T->node_nrows || !T->node_closed || !T->x || !T->target || !T->var) {
+      set_error("scuba_solve_batch: bad trace buffers (depth 1..8, all arrays set)");
+      return SCUBA_ERR_ARG;
+    }
+    mode = dev::MODE_TRACE;
+  } else if (opt->heuristic == SCUBA_HEUR_LEARNED) {
+    if (!opt->mlp_weights || opt->learned_depth < 0) {
+      set_error("scuba_solve_batch: learned branching needs mlp_weights and learned_depth >= 0");
+      return SCUBA_ERR_ARG;
+    }
+    mode = dev::MODE_LEARNED;
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
@@ -1192,6 +1463,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   int trail_smem = opt->trail_placement == 1 ? 1 : 0;
   (void)per_warp_s;
   size_t per_warp = trail_smem ? per_warp_s : per_warp_g;
+  if (mode == dev::MODE_LEARNED) per_warp += 32 * learn::NFEAT * sizeof(__nv_bfloat16);
   size_t smem = per_warp * wpb;
   while (wpb > 1 && smem > smem_cap) {
     wpb--;
@@ -1202,6 +1474,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
     return SCUBA_ERR_TOO_LARGE;
   }
   while (bps > 1 && (smem + 1024) * bps > sm_cap) bps--;
+  if (mode == dev::MODE_LEARNED) bps = std::min(bps, 4);
   const int64_t slots = (int64_t)S.sms * bps * wpb;
   const uint32_t ring_cap = 2048;
 
@@ -1216,6 +1489,12 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
       ensure(S.job_act, 4 * (size_t)ring_cap * vmax) ||
       ensure(S.prefix, 4 * (size_t)slots * dev::MAX_PREFIX) || ensure(S.ctrl, sizeof(dev::Ctrl))) {
     set_error("scuba_solve_batch: out of device memory for scratch");
+    return SCUBA_ERR_NOMEM;
+  }
+  if (mode == dev::MODE_TRACE &&
+      (ensure(S.lvlcnt, 4 * (size_t)slots * learn::MAX_TRACE_DEPTH * vmax) ||
+       ensure(S.lvl_node, 8 * (size_t)slots * learn::MAX_TRACE_DEPTH))) {
+    set_error("scuba_solve_batch: out of device memory for trace scratch");
     return SCUBA_ERR_NOMEM;
   }
   dev::Prep pr;
@@ -1292,15 +1571,44 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.trail_smem = trail_smem;
   sv.finish_ns = opt->finish_ns;
   sv.prof = reinterpret_cast<unsigned long long*>(opt->profile);
+  sv.mlp = static_cast<const learn::MlpWeights*>(opt->mlp_weights);
+  sv.learned_depth = opt->learned_depth;
+  sv.inst_num_inputs = opt->inst_num_inputs;
+  sv.trace_depth = 0;
+  sv.lvlcnt = nullptr;
+  sv.lvl_node = nullptr;
+  std::memset(&sv.tr, 0, sizeof(sv.tr));
+  if (mode == dev::MODE_TRACE) {
+    const scuba_trace* T = opt->trace;
+    sv.trace_depth = T->depth;
+    sv.split = 0;  // a traced subtree must be explored by one warp
+    sv.tr.cursor = reinterpret_cast<unsigned long long*>(T->counts);
+    sv.tr.max_nodes = T->max_nodes;
+    sv.tr.max_rows = T->max_rows;
+    sv.tr.node_inst = T->node_inst;
+    sv.tr.node_depth = T->node_depth;
+    sv.tr.node_row = T->node_row;
+    sv.tr.node_nrows = T->node_nrows;
+    sv.tr.node_closed = T->node_closed;
+    sv.tr.x = reinterpret_cast<__nv_bfloat16*>(T->x);
+    sv.tr.target = T->target;
+    sv.tr.var = T->var;
+    sv.lvlcnt = P<uint32_t>(S.lvlcnt);
+    sv.lvl_node = P<int64_t>(S.lvl_node);
+    cudaMemsetAsync(sv.lvlcnt, 0, 4 * (size_t)slots * learn::MAX_TRACE_DEPTH * vmax, st);
+    cudaMemsetAsync(sv.lvl_node, 0xff, 8 * (size_t)slots * learn::MAX_TRACE_DEPTH, st);
+  }
 
   dev::k_init_ring<<<16, 256, 0, st>>>(sv.ring, ring_cap);
   dev::k_init_inst<<<(n + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec, n);
   dev::k_start_clock<<<1, 1, 0, st>>>(sv.ctrl);
-  e = cudaFuncSetAttribute(dev::k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  auto kern = mode == dev::MODE_TRACE     ? dev::k_solve<dev::MODE_TRACE>
+              : mode == dev::MODE_LEARNED ? dev::k_solve<dev::MODE_LEARNED>
+                                          : dev::k_solve<dev::MODE_PLAIN>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
   if (opt->search_event_begin) cudaEventRecord((cudaEvent_t)opt->search_event_begin, st);
-  dev::k_solve<<<S.sms * bps, 32 * wpb, smem, st>>>(sv);
+  kern<<<S.sms * bps, 32 * wpb, smem, st>>>(sv);
   if (opt->search_event_end) cudaEventRecord((cudaEvent_t)opt->search_event_end, st);
   dev::k_finalize<<<(n + 255) / 256, 256, 0, st>>>(sv);
   e = cudaGetLastError();
@@ -1388,7 +1696,7 @@ extern "C" void scuba_release(void) {
   Scratch& S = it->second;
   Buf* all[] = {&S.occ_base, &S.norm, &S.occ_cnt, &S.occ_begin, &S.ent, &S.units, &S.nunits,
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
-                &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.h_icb, &S.h_cb, &S.h_lits, &S.h_nv, &S.h_vb,
+                &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node, &S.h_icb, &S.h_cb, &S.h_lits, &S.h_nv, &S.h_vb,
                 &S.h_verdict, &S.h_model, &S.h_stats};
   for (Buf* x : all) {
     if (x->p) cudaFree(x->p);
@@ -1590,10 +1898,10 @@ extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verd
   dev::k_init_ring<<<4, 256, 0, st>>>(sv.ring, ring_cap);
   dev::k_init_inst<<<(n + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec, n);
   dev::k_start_clock<<<1, 1, 0, st>>>(sv.ctrl);
-  e = cudaFuncSetAttribute(dev::k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  e = cudaFuncSetAttribute(dev::k_solve<dev::MODE_PLAIN>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
-  dev::k_solve<<<sms, 32 * wpb, smem, st>>>(sv);
+  dev::k_solve<dev::MODE_PLAIN><<<sms, 32 * wpb, smem, st>>>(sv);
   dev::k_finalize<<<(n + 255) / 256, 256, 0, st>>>(sv);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("kernel launch", e);

@@ -240,6 +240,16 @@ def random_3sat(seed: int, n_lo: int = 200, n_hi: int = 400, ratio: float = 4.26
     return nv, out
 
 
+def config4_split(count_train: int = 2048, count_test: int = 4096, w: int = 16):
+    """Learned-branching workload: the config-2 generator with a seed split,
+    even seeds for training traces and odd seeds for the held-out test."""
+    base = SEED_BASE[4]
+    tr = [config2_params(base + 2 * i, w) for i in range(count_train)]
+    te = [config2_params(base + 2 * i + 1, w) for i in range(count_test)]
+    return ([partition_query(**p).to_array() for p in tr], tr,
+            [partition_query(**p).to_array() for p in te], te)
+
+
 def config5_sat(count: int = 10000, seed0: int | None = None):
     seed0 = SEED_BASE[5] if seed0 is None else seed0
     return [random_3sat(seed0 + i) for i in range(count)]
