@@ -9,7 +9,11 @@ persistent DPLL search + verdict finalisation. Verdicts are checked
 bit-exactly against stored oracle verdicts after timing.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--heuristic activity|learned]
+                    [--heuristic plain|learned|both]
+
+The plain arm (activity branching) gives the headline value; the learned arm
+(the incidence MLP trained beforehand on decision traces of held-out seeds)
+is reported beside it under "arms", with identical verdicts required.
 
 Under torchrun each rank solves its own batch (different seeds): weak
 scaling, no collective on the data path.
@@ -168,6 +172,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _train_network(api, B, dev, args):
+    """Decision traces of the plain search on the training split (even seeds
+    of the config-2 generator), then Adam on the GPU. Not timed as a step."""
+    from workloads import queries
+    t0 = time.perf_counter()
+    tr_irs, _, _, _ = queries.config4_split(args.train_queries, 0, w=args.width)
+    enc = B.scuba_encode_batch(tr_irs)
+    db = api.DeviceBatch(enc, dev)
+    trace, _, _ = api.record_trace(db, depth=args.learned_depth, max_nodes=1 << 17,
+                                   max_rows=1 << 25, decision_budget=args.trace_budget,
+                                   time_budget_ms=300000)
+    nodes, rows = trace.used()
+    net = api.Mlp(seed=3, device=dev)
+    losses = net.train(trace, epochs=args.epochs, batch_nodes=64, lr=3e-3)
+    torch_sync = __import__("torch").cuda.synchronize
+    torch_sync()
+    info = {"train_queries": args.train_queries, "trace_nodes": nodes, "trace_rows": rows,
+            "epochs": args.epochs, "loss_first": losses[0] if losses else None,
+            "loss_last": losses[-1] if losses else None,
+            "train_s": time.perf_counter() - t0, "learned_depth": args.learned_depth}
+    del trace
+    return net, info
+
+
+def _timed_arm(api, B, db, dev, stream, count, heur_opts, args, use_graph=True):
+    """W warm-up solves, then K timed steps (CUDA-graph replays of one solve).
+    Returns per-arm timings, counters and the last verdicts."""
+    import torch
+    stats = torch.zeros((count, B.SCUBA_NSTATS), dtype=torch.int64, device=dev)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record(stream)
+    ev[1].record(stream)
+    verdict = torch.empty(count, dtype=torch.uint8, device=dev)
+
+    def launch(st_tensor, events):
+        o = api.options(stats=st_tensor, time_budget_ms=300000, events=events,
+                        num_inputs=db.num_inputs, **heur_opts)
+        B.scuba_solve_batch_ex(db.struct(), verdict.data_ptr(), None, stream.cuda_stream, o)
+
+    for _ in range(args.warmup):
+        launch(None, None)
+    rc = api.status(stream)
+    assert rc == 0, f"warm-up solve failed: {rc} {B.last_error()}"
+    graph = None
+    if use_graph:
+        # one captured solve (no timing events inside: events recorded in a
+        # capture cannot be read back); replays are timed from outside
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            launch(stats, None)
+        torch.cuda.synchronize()
+        stats.zero_()
+    ms_search = []
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        if graph is not None:
+            graph.replay()
+        else:
+            launch(stats, ev)
+            ev[1].synchronize()
+            ms_search.append(ev[0].elapsed_time(ev[1]))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    rc = api.status(stream)
+    assert rc == 0, f"timed solve failed: {rc}"
+    st = stats.cpu().numpy().astype(np.float64) / args.steps
+    if graph is not None:  # search-kernel time from one direct launch
+        launch(None, ev)
+        ev[1].synchronize()
+        ms_search.append(ev[0].elapsed_time(ev[1]))
+    return {"ms_total": t_start.elapsed_time(t_end), "ms_search": ms_search, "stats": st,
+            "verdict": verdict.cpu().numpy().copy()}
+
+
 def run_ours(args):
     import torch
     ws, rank = _dist()
@@ -188,62 +268,41 @@ def run_ours(args):
     t_enc = time.perf_counter() - t_enc
     db = api.DeviceBatch(enc, dev)
     torch.cuda.synchronize()
-    heur = B.SCUBA_HEUR_LEARNED if args.heuristic == "learned" else B.SCUBA_HEUR_ACTIVITY
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)  # graphs cannot be captured on the legacy stream
 
-    def step(stats=None, events=None):
-        verdict = torch.empty(count, dtype=torch.uint8, device=dev)
-        o = api.options(heuristic=heur, stats=stats, time_budget_ms=300000, events=events)
-        B.scuba_solve_batch_ex(db.struct(), verdict.data_ptr(), None, stream.cuda_stream, o)
-        return verdict
+    arms = ["plain", "learned"] if args.heuristic == "both" else [args.heuristic]
+    net, train_info = None, None
+    if "learned" in arms:
+        net, train_info = _train_network(api, B, dev, args)
 
-    for _ in range(args.warmup):
-        step()
-    rc = api.status(stream)
-    assert rc == 0, f"warm-up solve failed: {rc} {B.last_error()}"
-
-    # timed region: K steps, per-step search-kernel events
-    stats = torch.zeros((count, B.SCUBA_NSTATS), dtype=torch.int64, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for a, b in ev:  # create the underlying events on this stream
-        a.record(stream)
-        b.record(stream)
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    verdicts = []
+    results = {}
     with ClockSampler(local) as clk:
-        t_start.record(stream)
-        for k in range(args.steps):
-            verdicts.append(step(stats=stats, events=ev[k]))
-        t_end.record(stream)
-        torch.cuda.synchronize()
-    rc = api.status(stream)
-    assert rc == 0, f"timed solve failed: {rc}"
+        for arm in arms:
+            opts = {}
+            if arm == "learned":
+                opts = dict(heuristic=B.SCUBA_HEUR_LEARNED, mlp_weights=net.weights,
+                            learned_depth=args.learned_depth)
+            results[arm] = _timed_arm(api, B, db, dev, stream, count, opts, args,
+                                      use_graph=args.graph)
     if ws > 1:
         torch.distributed.barrier()
-    ms_total = t_start.elapsed_time(t_end)
-    ms_search = [a.elapsed_time(b) for a, b in ev]
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+        for arm in arms:
+            t = torch.tensor([results[arm]["ms_total"]], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            results[arm]["ms_total"] = float(t.item())
 
-    # parity after timing
-    v = verdicts[-1].cpu().numpy()
-    parity = None
+    # parity after timing: both arms bit-exact against the stored oracle verdicts
+    parity = {}
     if rank == 0 and count == 4096 and args.width == 16:
         stored = _stored_verdicts()
-        parity = int((v == stored).sum())
-        assert parity == count, f"verdicts differ from the oracle on {count - parity} queries"
-    st = stats.cpu().numpy().astype(np.float64) / args.steps
-    props = st[:, 2].sum()
-    visits = st[:, 3].sum()
-    alg_bytes = 16 * props + 8 * visits + 4 * st[:, 4].sum() + 4 * st[:, 5].sum()
-    ms_step = ms_total / args.steps
-    search_ms = float(np.mean(ms_search))
+        for arm in arms:
+            ok = int((results[arm]["verdict"] == stored).sum())
+            assert ok == count, f"{arm}: verdicts differ from the oracle on {count - ok} queries"
+            parity[arm] = f"{ok}/{count} bit-exact"
+    if len(arms) == 2:
+        assert (results["plain"]["verdict"] == results["learned"]["verdict"]).all()
 
     # end to end through the host entry point (host buffers, copies inside)
     h_verdict = np.zeros(count, np.uint8)
@@ -251,7 +310,7 @@ def run_ours(args):
                       enc.inst_clause_begin.ctypes.data, enc.clause_begin.ctypes.data,
                       enc.lits.ctypes.data, enc.inst_num_vars.ctypes.data,
                       enc.inst_var_begin.ctypes.data)
-    o = api.options(heuristic=heur, time_budget_ms=300000)
+    o = api.options(time_budget_ms=300000)
     B.scuba_solve_batch_host(hb, h_verdict, None, stream.cuda_stream, o)  # warm
     e2e_t = []
     for _ in range(max(1, min(args.steps, 3))):
@@ -260,40 +319,57 @@ def run_ours(args):
         rc = B.scuba_solve_batch_host(hb, h_verdict, None, stream.cuda_stream, o)
         e2e_t.append(time.perf_counter() - t0)
         assert rc == 0
-    h2d = db.h2d_bytes
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
 
+    def arm_summary(r):
+        st = r["stats"]
+        ms_step = r["ms_total"] / args.steps
+        props = st[:, 2].sum()
+        alg_bytes = 16 * props + 8 * st[:, 3].sum() + 4 * st[:, 4].sum() + 4 * st[:, 5].sum()
+        search_ms = float(np.mean(r["ms_search"]))
+        return {"value": count * ws / (ms_step * 1e-3), "unit": "verdicts/s",
+                "ms_per_step": ms_step, "propagations_per_s": props * ws / (ms_step * 1e-3),
+                "decisions_per_step": float(st[:, 0].sum()),
+                "search_ms": search_ms, "search_ms_steps": r["ms_search"],
+                "alg_bytes": float(alg_bytes)}
+
+    summ = {arm: arm_summary(results[arm]) for arm in arms}
+    head = summ[arms[0]]
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = alg_bytes / (search_ms * 1e-3) / 1e9
+    achieved = head["alg_bytes"] / (head["search_ms"] * 1e-3) / 1e9
     line = {
         "metric": METRIC,
-        "value": count * ws / (ms_step * 1e-3),
+        "value": head["value"],
         "unit": "verdicts/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step,
+        "ms_per_step": head["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "heuristic": args.heuristic,
-        "propagations_per_s": props * ws / (ms_step * 1e-3),
-        "config": {"workload": WORKLOAD, "queries_per_gpu": count, "input_bits": 16,
+        "heuristic": arms[0],
+        "propagations_per_s": head["propagations_per_s"],
+        "config": {"workload": WORKLOAD, "queries_per_gpu": count, "input_bits": args.width,
                    "clauses_total": enc.total_clauses, "literals_total": enc.total_lits,
-                   "vars_total": enc.total_vars, "l2": "inputs larger than L2 (CSR + occurrence "
-                   "lists > 1 GB)", "encode_s": t_enc, "parity": f"{parity}/{count} bit-exact"},
+                   "vars_total": enc.total_vars,
+                   "l2": "inputs larger than L2 (CSR + occurrence lists > 1 GB)",
+                   "encode_s": t_enc, "cuda_graph": args.graph, "parity": parity},
+        "arms": summ,
         "e2e": {"value": count / float(np.median(e2e_t)), "unit": "verdicts/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": count},
+                "h2d_bytes_per_step": db.h2d_bytes, "d2h_bytes_per_step": count},
         "gpu_launches": 10 * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "kernel": "k_solve",
-                     "peak_source": src, "search_ms": search_ms},
+                     "peak_source": src, "search_ms": head["search_ms"]},
         "clocks": clk.summary(),
     }
+    if train_info:
+        line["learned_training"] = train_info
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(irs, target_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -307,7 +383,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--heuristic", default="activity", choices=["activity", "learned"])
+    ap.add_argument("--heuristic", default="both", choices=["plain", "learned", "both"])
+    ap.add_argument("--graph", action="store_true",
+                    help="replay each step from a captured CUDA graph")
+    ap.add_argument("--learned-depth", type=int, default=6)
+    ap.add_argument("--train-queries", type=int, default=2048)
+    ap.add_argument("--trace-budget", type=int, default=20000,
+                    help="decision budget per training query while tracing")
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--queries", type=int, default=4096,

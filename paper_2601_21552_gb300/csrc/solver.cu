@@ -1331,6 +1331,7 @@ struct Scratch {
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
   int32_t last_status = 0;
+  int smem_set[3] = {0, 0, 0};  // dynamic shared memory granted per search mode
 };
 
 std::map<int, Scratch>& scratch_map() {
@@ -1605,8 +1606,14 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   auto kern = mode == dev::MODE_TRACE     ? dev::k_solve<dev::MODE_TRACE>
               : mode == dev::MODE_LEARNED ? dev::k_solve<dev::MODE_LEARNED>
                                           : dev::k_solve<dev::MODE_PLAIN>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
+  // raise the dynamic shared-memory limit only when it grows, so that a
+  // repeated call (for example while a CUDA graph is being captured) issues
+  // no attribute change
+  if ((int)smem > S.smem_set[mode]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
+    S.smem_set[mode] = (int)smem;
+  }
   if (opt->search_event_begin) cudaEventRecord((cudaEvent_t)opt->search_event_begin, st);
   kern<<<S.sms * bps, 32 * wpb, smem, st>>>(sv);
   if (opt->search_event_end) cudaEventRecord((cudaEvent_t)opt->search_event_end, st);

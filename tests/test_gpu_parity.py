@@ -191,3 +191,29 @@ def test_empty_batch(api):
     from paper_2601_21552_gb300 import binding as B
     b = B.make_batch(0, 0, 0, 0, 0, None, None, None, None, None)
     assert B.scuba_solve_batch(b, None, None, None) == 0
+
+
+def test_solve_captured_in_cuda_graph(api):
+    """The whole solve (prep kernels, persistent search, finalize) captured
+    once in a CUDA graph and replayed: same verdicts as a direct launch."""
+    from paper_2601_21552_gb300 import binding as B
+    irs, _ = queries.config2(512, w=10)
+    enc = B.scuba_encode_batch(irs)
+    db = api.DeviceBatch(enc, "cuda")
+    s = torch.cuda.Stream()
+    v = torch.empty(db.n, dtype=torch.uint8, device="cuda")
+    o = api.options(time_budget_ms=60000, num_inputs=db.num_inputs)
+    with torch.cuda.stream(s):
+        B.scuba_solve_batch_ex(db.struct(), v.data_ptr(), None, s.cuda_stream, o)  # warm scratch
+    assert B.scuba_sync_status(s.cuda_stream) == 0
+    ref = v.cpu().numpy().copy()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        B.scuba_solve_batch_ex(db.struct(), v.data_ptr(), None, s.cuda_stream, o)
+    for _ in range(2):
+        v.fill_(9)
+        g.replay()
+        torch.cuda.synchronize()
+        assert B.scuba_sync_status(s.cuda_stream) == 0
+        assert (v.cpu().numpy() == ref).all()
+    assert (ref == oracle.solve_queries(irs)["verdict"]).all()
