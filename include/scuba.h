@@ -49,7 +49,10 @@ enum {
   SCUBA_ERR_TIMEOUT = -4,   /* time budget reached; unfinished instances UNKNOWN */
   SCUBA_ERR_MALFORMED = -5, /* literal 0 or |literal| > num_vars, bad offsets */
   SCUBA_ERR_ABORTED = -6,   /* the caller's abort flag was raised */
-  SCUBA_ERR_TOO_LARGE = -7  /* an instance exceeds the solver's size limits */
+  SCUBA_ERR_TOO_LARGE = -7  /* an instance exceeds the solver's size limits: max_vars
+                               < 2^29, fewer than 2^32 literals per instance, and the
+                               2-bit assignment of max_vars variables must fit a
+                               warp's share of shared memory (about 900k variables) */
 };
 
 /* Branching heuristics (Sec. VIII-style extensions are not in the paper; the
@@ -257,6 +260,11 @@ int scuba_encoded_inputs(const scuba_encoded* enc, int64_t* inst_input_begin,
                          int32_t* input_width, int32_t* input_var);
 
 void scuba_encoded_free(scuba_encoded* enc);
+
+/* Frees the clause storage of an encoded batch once its CSR has been copied
+   out (large batches hold tens of GB); sizes, input maps and
+   scuba_verify_batch keep working, scuba_encoded_copy then fails. */
+int scuba_encoded_release_clauses(scuba_encoded* enc);
 
 /*
  * Re-verifies every SAT verdict on the host: decodes the input words of the

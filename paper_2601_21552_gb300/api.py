@@ -47,6 +47,38 @@ class DeviceBatch:
         ninp = (csum[iib[1:]] - csum[iib[:-1]]).astype(np.int32) if self.n else np.zeros(1, np.int32)
         self.num_inputs = up(ninp if self.n else np.zeros(1, np.int32))
 
+    @classmethod
+    def from_csr(cls, icb, cb, lits, nv, vb, num_inputs=None, device="cuda", pin=True):
+        """A device batch from host CSR arrays (inst_clause_begin, clause_begin,
+        lits, inst_num_vars, inst_var_begin), e.g. DIMACS-style CNFs."""
+        class _Enc:
+            pass
+        e = _Enc()
+        e.n = len(nv)
+        e.inst_clause_begin = np.ascontiguousarray(icb, np.int64)
+        e.clause_begin = np.ascontiguousarray(cb, np.int64)
+        e.lits = np.ascontiguousarray(lits, np.int32)
+        e.inst_num_vars = np.ascontiguousarray(nv, np.int32)
+        e.inst_var_begin = np.ascontiguousarray(vb, np.int64)
+        e.total_clauses = len(cb) - 1
+        e.total_lits = int(cb[-1]) if len(cb) else 0
+        e.total_vars = int(vb[-1]) if len(vb) else 0
+        e.max_vars = int(nv.max()) if len(nv) else 0
+        ni = np.zeros(max(e.n, 1), np.int32) if num_inputs is None else np.asarray(num_inputs, np.int32)
+        e.inputs = lambda: (np.zeros(e.n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
+        obj = cls(e, device, pin)
+        obj.num_inputs = torch.from_numpy(ni).to(torch.device(device))
+        return obj
+
+    def lpt_order(self) -> torch.Tensor:
+        """Largest instances first (longest-processing-time order by clause
+        count), as a device int32 permutation for scuba_options.order."""
+        if getattr(self, "_lpt", None) is None:
+            nc = np.diff(self.enc.inst_clause_begin)
+            perm = np.argsort(-nc, kind="stable").astype(np.int32)
+            self._lpt = torch.from_numpy(perm).to(self.icb.device)
+        return self._lpt
+
     def struct(self) -> B.scuba_cnf_batch:
         return B.make_batch(self.n, self.max_vars, self.total_clauses, self.total_lits,
                             self.total_vars, self.icb.data_ptr(), self.cb.data_ptr(),
@@ -126,6 +158,8 @@ def solve(db: DeviceBatch, want_model: bool = True, stats: bool = True,
     stats i64[n,3] | None) device tensors. Asynchronous: call
     ``status(stream)`` to wait and collect the device status."""
     dev = db.icb.device
+    if opts.get("order") == "lpt":
+        opts["order"] = db.lpt_order()
     verdict = torch.empty(max(db.n, 1), dtype=torch.uint8, device=dev)
     model = torch.zeros(max(db.total_vars, 1), dtype=torch.uint8, device=dev) if want_model else None
     st = torch.zeros((max(db.n, 1), B.SCUBA_NSTATS), dtype=torch.int64, device=dev) if stats else None

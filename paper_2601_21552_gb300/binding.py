@@ -86,6 +86,7 @@ _sig("scuba_encoded_sizes", _i32, [_vp, _vp])
 _sig("scuba_encoded_copy", _i32, [_vp, _vp, _vp, _vp, _vp, _vp])
 _sig("scuba_encoded_inputs", _i32, [_vp, _vp, _vp, _vp])
 _sig("scuba_encoded_free", None, [_vp])
+_sig("scuba_encoded_release_clauses", _i32, [_vp])
 _sig("scuba_verify_batch", _i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp])
 _sig("scuba_mlp_layout", _i32, [_vp])
 _sig("scuba_mlp_init", _i32, [_vp, _vp, ctypes.c_uint64, _vp])
@@ -99,7 +100,8 @@ EXPORTED = [
     "scuba_options_init", "scuba_solve_batch", "scuba_solve_batch_ex",
     "scuba_solve_batch_host", "scuba_solve_batch_noalloc", "scuba_sync_status", "scuba_release", "scuba_last_error",
     "scuba_version", "scuba_abi_sizes", "scuba_encode_batch", "scuba_encoded_sizes", "scuba_encoded_copy",
-    "scuba_encoded_inputs", "scuba_encoded_free", "scuba_verify_batch",
+    "scuba_encoded_inputs", "scuba_encoded_free", "scuba_encoded_release_clauses",
+    "scuba_verify_batch",
     "scuba_mlp_layout", "scuba_mlp_init", "scuba_mlp_pack", "scuba_mlp_forward",
     "scuba_mlp_grad", "scuba_mlp_train",
 ]
@@ -176,6 +178,10 @@ class Encoded:
                                          _np_ptr(var)), "scuba_encoded_inputs")
         nwords = int(iib[-1])
         return iib, widths[:nwords], var[:self.total_input_bits]
+
+    def release_clauses(self) -> None:
+        """Free the library-side clause storage (the numpy CSR copies stay)."""
+        _check(_lib.scuba_encoded_release_clauses(self.handle), "scuba_encoded_release_clauses")
 
     def __del__(self):
         if getattr(self, "handle", None):

@@ -19,6 +19,8 @@ void set_error(const std::string& msg) { g_err = msg; }
 
 struct scuba_encoded {
   std::vector<scuba::HostCnf> cnf;
+  bool released = false;  // clause storage freed; sizes/inputs/verify still work
+  int64_t clauses = 0, lits = 0;
 };
 
 namespace {
@@ -76,16 +78,18 @@ int scuba_encode_batch(int32_t n, const int64_t* irs, const int64_t* ir_offsets,
     delete enc;
     return SCUBA_ERR_MALFORMED;
   }
+  for (auto& c : enc->cnf) {
+    enc->clauses += (int64_t)c.clause_begin.size() - 1;
+    enc->lits += (int64_t)c.lits.size();
+  }
   *out = enc;
   return SCUBA_OK;
 }
 
 int scuba_encoded_sizes(const scuba_encoded* enc, int64_t* s) {
   if (!enc || !s) return SCUBA_ERR_ARG;
-  int64_t C = 0, L = 0, V = 0, mx = 0, bits = 0;
+  int64_t C = enc->clauses, L = enc->lits, V = 0, mx = 0, bits = 0;
   for (auto& c : enc->cnf) {
-    C += (int64_t)c.clause_begin.size() - 1;
-    L += (int64_t)c.lits.size();
     V += c.nvars;
     mx = std::max<int64_t>(mx, c.nvars);
     bits += (int64_t)c.in_map.size();
@@ -102,6 +106,10 @@ int scuba_encoded_sizes(const scuba_encoded* enc, int64_t* s) {
 int scuba_encoded_copy(const scuba_encoded* enc, int64_t* icb, int64_t* cb, int32_t* lits,
                        int32_t* nv, int64_t* vb) {
   if (!enc || !icb || !cb || !lits || !nv || !vb) return SCUBA_ERR_ARG;
+  if (enc->released) {
+    scuba::set_error("scuba_encoded_copy: clause storage was released");
+    return SCUBA_ERR_ARG;
+  }
   const int n = (int)enc->cnf.size();
   // offsets first (sequential prefix sums), then the bulk copy in parallel
   std::vector<int64_t> lit_base(n + 1, 0);
@@ -138,6 +146,16 @@ int scuba_encoded_inputs(const scuba_encoded* enc, int64_t* iib, int32_t* width,
 }
 
 void scuba_encoded_free(scuba_encoded* enc) { delete enc; }
+
+int scuba_encoded_release_clauses(scuba_encoded* enc) {
+  if (!enc) return SCUBA_ERR_ARG;
+  for (auto& c : enc->cnf) {
+    std::vector<int64_t>().swap(c.clause_begin);
+    std::vector<int32_t>().swap(c.lits);
+  }
+  enc->released = true;
+  return SCUBA_OK;
+}
 
 int scuba_verify_batch(const scuba_encoded* enc, const int64_t* irs, const int64_t* ir_offsets,
                        const uint8_t* verdict, const uint8_t* model, int32_t nthreads,

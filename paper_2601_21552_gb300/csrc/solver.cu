@@ -124,6 +124,9 @@ __global__ void k_occ_base(Prep P) {
     if (P.icb[i] > P.icb[i + 1]) bad_header = 1;
     uint32_t f = 0;
     if (v < 0 || v > P.vmax) f |= F_BAD;
+    // occurrence offsets are 32-bit within an instance
+    const int64_t ca = P.icb[i], cz = P.icb[i + 1];
+    if (ca >= 0 && cz >= ca && cz <= P.C && P.cb[cz] - P.cb[ca] >= (1LL << 32)) f |= F_BAD;
     if (P.vb[i] < 0 || P.vb[i] + (int64_t)(v < 0 ? 0 : v) > P.total_vars) f |= F_BAD;
     if (f) atomicOr(&P.flags[i], f);
     s += 2 * (int64_t)clamp_nv(v, P.vmax) + 1;
@@ -1416,8 +1419,8 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
     set_error("scuba_solve_batch: unknown heuristic");
     return SCUBA_ERR_ARG;
   }
-  if (b->max_vars >= (1 << 29) || b->total_lits >= (1LL << 32)) {
-    set_error("scuba_solve_batch: instance too large");
+  if (b->max_vars >= (1 << 29)) {
+    set_error("scuba_solve_batch: instance too large (max_vars >= 2^29)");
     return SCUBA_ERR_TOO_LARGE;
   }
   int mode = dev::MODE_PLAIN;

@@ -1,0 +1,158 @@
+"""Full-size uneven workloads on the GPU.
+
+* 65,536 grown queries (widths 8/16/32, clause counts log-uniform in
+  [500, 200k], largest first) solved in one persistent launch with a
+  per-instance decision budget: every SAT model re-verified on the host
+  against the original integer constraints, and verdicts compared with the
+  oracle on a sample it can decide one by one.
+* 10,000 uniform random 3-SAT instances (n in [200, 400], ratio 4.26) mixed
+  with 10,000 bounds queries at 32 bits in one batch (a propagation stress
+  test with a decision budget): 3-SAT models checked against the clauses,
+  bounds verdicts against the closed form, 3-SAT verdicts against the oracle
+  where both decide.
+
+Plain DPLL cannot refute every multiplier-heavy query within a budget; the
+UNKNOWN counts are reported, never hidden."""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from closed_forms import bounds_algebra
+from workloads import queries
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def libs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_21552_gb300 import build
+    build.build()
+    from paper_2601_21552_gb300 import api, binding
+    return api, binding
+
+
+def _report(name, d):
+    print(name, json.dumps(d))
+    out = os.environ.get("SCUBA_REPORT_DIR")
+    if out:
+        with open(os.path.join(out, name + ".json"), "w") as f:
+            json.dump(d, f)
+
+
+def test_uneven_batch_65536(libs):
+    api, B = libs
+    t0 = time.perf_counter()
+    irs, meta = queries.config3(65536)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    enc = B.scuba_encode_batch(irs)
+    t_enc = time.perf_counter() - t0
+    enc.release_clauses()
+    db = api.DeviceBatch(enc, "cuda", pin=False)
+    torch.cuda.synchronize()
+    budget = 100_000
+    t0 = time.perf_counter()
+    v, m, st = api.solve(db, order="lpt", decision_budget=budget, time_budget_ms=600000)
+    rc = api.status()
+    t_solve = time.perf_counter() - t0
+    assert rc == 0, B.last_error()
+    vh, mh, sth = v.cpu().numpy(), m.cpu().numpy(), st.cpu().numpy()
+    fails, ok = B.scuba_verify_batch(enc, vh, mh)
+    assert fails == 0
+    # oracle on a sample it can decide: the smallest queries and a random draw
+    nc = np.diff(enc.inst_clause_begin)
+    rng = np.random.default_rng(0)
+    small = np.argsort(nc, kind="stable")[:64]
+    mid = rng.choice(np.flatnonzero(nc < 20000), 64, replace=False)
+    sample = np.unique(np.concatenate([small, mid]))
+    ref = oracle.solve_queries([irs[i] for i in sample], budget=300000)["verdict"]
+    both = (ref != 2) & (vh[sample] != 2)
+    assert (ref[both] == vh[sample][both]).all()
+    w = np.array([x["w"] for x in meta])
+    rep = {"queries": 65536, "clauses_total": int(enc.total_clauses),
+           "literals_total": int(enc.total_lits), "clauses_p50": int(np.median(nc)),
+           "clauses_max": int(nc.max()), "decision_budget": budget,
+           "sat": int((vh == 1).sum()), "unsat": int((vh == 0).sum()),
+           "unknown": int((vh == 2).sum()),
+           "unknown_by_width": {str(x): int(((vh == 2) & (w == x)).sum()) for x in (8, 16, 32)},
+           "gen_s": t_gen, "encode_s": t_enc, "solve_s": t_solve,
+           "verdicts_per_s": 65536 / t_solve,
+           "propagations_per_s": float(sth[:, 2].sum()) / t_solve,
+           "oracle_sample": int(len(sample)), "oracle_sample_both_decided": int(both.sum())}
+    _report("uneven_65536", rep)
+
+
+def _pack_mixed(sat, enc):
+    """Concatenate raw 3-SAT instances and an encoded query batch into one CSR."""
+    icb, cb, lits, nv = [0], [np.zeros(1, np.int64)], [], []
+    base_c, base_l = 0, 0
+    for n, l in sat:
+        m = len(l)
+        cb.append(base_l + 3 * np.arange(1, m + 1, dtype=np.int64))
+        lits.append(l.reshape(-1))
+        base_c += m
+        base_l += 3 * m
+        icb.append(base_c)
+        nv.append(n)
+    e_icb = enc.inst_clause_begin[1:] + base_c
+    cb.append(enc.clause_begin[1:] + base_l)
+    lits.append(enc.lits)
+    icb = np.concatenate([np.array(icb, np.int64), e_icb])
+    nv = np.concatenate([np.array(nv, np.int32), enc.inst_num_vars])
+    vb = np.concatenate([[0], np.cumsum(nv, dtype=np.int64)])
+    return icb, np.concatenate(cb), np.concatenate(lits).astype(np.int32), nv, vb
+
+
+def test_bcp_stress_mixed_batch(libs):
+    api, B = libs
+    sat = queries.config5_sat(10000)
+    b_irs, b_params = queries.config5_bounds(10000)
+    enc = B.scuba_encode_batch(b_irs)
+    icb, cb, lits, nv, vb = _pack_mixed(sat, enc)
+    db = api.DeviceBatch.from_csr(icb, cb, lits, nv, vb)
+    torch.cuda.synchronize()
+    budget = 200_000
+    t0 = time.perf_counter()
+    v, m, st = api.solve(db, decision_budget=budget, time_budget_ms=600000)
+    rc = api.status()
+    t_solve = time.perf_counter() - t0
+    assert rc == 0, B.last_error()
+    vh, mh, sth = v.cpu().numpy(), m.cpu().numpy(), st.cpu().numpy()
+    # 3-SAT models satisfy every clause
+    for i in np.flatnonzero(vh[:10000] == 1):
+        n, l = sat[i]
+        mv = mh[vb[i]:vb[i] + n].astype(bool)
+        val = np.where(l > 0, mv[np.abs(l) - 1], ~mv[np.abs(l) - 1])
+        assert val.any(axis=1).all(), i
+    # bounds queries: models verified, verdicts against the closed form
+    vb_q, mb_q = vh[10000:], mh[vb[10000]:]
+    fails, ok = B.scuba_verify_batch(enc, vb_q, mb_q)
+    assert fails == 0
+    cf = np.array([1 if bounds_algebra(**p) else 0 for p in b_params])
+    dec = vb_q != 2
+    assert (vb_q[dec] == cf[dec]).all()
+    # 3-SAT against the oracle where both decide (sample)
+    idx = np.random.default_rng(1).choice(10000, 200, replace=False)
+    ocnf = [oracle.CNF(sat[i][0], np.arange(0, 3 * len(sat[i][1]) + 1, 3),
+                       sat[i][1].reshape(-1)) for i in idx]
+    ref = oracle.solve_cnfs(ocnf, budget=budget)["verdict"]
+    both = (ref != 2) & (vh[idx] != 2)
+    assert (ref[both] == vh[idx][both]).all()
+    rep = {"instances": 20000, "random_3sat": 10000, "bounds_32bit": 10000,
+           "decision_budget": budget, "solve_s": t_solve,
+           "sat_3sat": int((vh[:10000] == 1).sum()), "unsat_3sat": int((vh[:10000] == 0).sum()),
+           "unknown_3sat": int((vh[:10000] == 2).sum()),
+           "sat_bounds": int((vb_q == 1).sum()), "unsat_bounds": int((vb_q == 0).sum()),
+           "unknown_bounds": int((vb_q == 2).sum()),
+           "propagations": int(sth[:, 2].sum()),
+           "propagations_per_s": float(sth[:, 2].sum()) / t_solve,
+           "oracle_sample_both_decided": int(both.sum())}
+    _report("bcp_stress_20000", rep)

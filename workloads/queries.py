@@ -107,30 +107,26 @@ def config2(count: int = 4096, w: int = 16, seed0: int | None = None):
 # Grown (uneven) queries.
 # --------------------------------------------------------------------------
 
-def _structure_cost(kind: str, w: int) -> int:
-    """Size proxy in bit-cells (a p x q variable multiply counts p*q cells, a
-    p-bit add or compare p cells). Used only to steer template growth toward
-    a target; the actual encoded size is whatever the encoder produces."""
-    if kind == "dim":      # idx' = idx * bd + t  (t < bd)
-        return 2 * w * w + 6 * w
-    if kind == "cube":     # size' = size * (N+1)^3 * E * 3
-        return 6 * w * w + 10 * w
-    if kind == "rows":     # size' = size * R, offset' = offset * R + col (col < R)
-        return 4 * w * w + 6 * w
-    raise ValueError(kind)
+CELLS_PER_CLAUSE = 1.0 / 14.0   # size proxy calibration (cells per encoded clause)
 
 
-def grown_query(seed: int, target_cells: int | None = None) -> tuple[IR, dict]:
-    """One config-3 query: width from {8,16,32} (p = .4/.4/.2), size target
-    log-uniform, grown from a bounds or partition base by adding dimensions,
-    cubic size factors and row-major scalings."""
+def grown_query(seed: int, target_clauses: float | None = None) -> tuple[IR, dict]:
+    """One config-3 query: width from {8,16,32} (p = .4/.4/.2), a clause-count
+    target log-uniform in [500, 200k], grown from a bounds or partition base by
+    adding thread-block dimensions (idx*bd + t), row-major scalings (idx*R +
+    col) and cubic size factors ((N+1)^3*E*3, Fig. 1) while a size proxy stays
+    within the target.
+
+    The proxy counts bit-cells: a product of words of widths p and q costs
+    p*q cells, a p-bit sum or comparison p cells; widths follow exact
+    arithmetic (p*q has p+q bits). It only steers growth; the encoded size is
+    whatever the encoder produces and is reported as such."""
     r = SplitMix64(seed)
     u = r.uniform()
     w = 8 if u < 0.4 else (16 if u < 0.8 else 32)
-    if target_cells is None:
-        # log-uniform clause target in [500, 200k]; ~20 clauses per cell
-        tgt = math.exp(math.log(500) + r.uniform() * (math.log(200000) - math.log(500)))
-        target_cells = max(1, int(tgt / 20))
+    if target_clauses is None:
+        target_clauses = math.exp(math.log(500) + r.uniform() * (math.log(200000) - math.log(500)))
+    budget = target_clauses * CELLS_PER_CLAUSE
     k1, k0, a, c = r.randint(1, 4), r.randint(0, 7), r.randint(1, 4), r.randint(0, 7)
     guard = r.bernoulli(0.5)
     use_part = r.bernoulli(0.3)
@@ -146,32 +142,46 @@ def grown_query(seed: int, target_cells: int | None = None) -> tuple[IR, dict]:
     idx = ir.add(ir.mul(bid, bdim), tid)
     limit = n                      # what the guard bounds idx by
     size = ir.add(ir.mul(ir.const(k1), n), ir.const(k0))
-    cells = 2 * w * w + 8 * w
+    w_idx, w_lim, w_size = 2 * w + 1, w, w + 3
+    cells = w * w + 6 * w
     structs = []
-    # grow until the proxy reaches the target (the smallest template is kept)
-    while True:
-        choices = ["dim", "cube", "rows"]
-        kind = choices[r.randint(0, 2)]
-        cost = _structure_cost(kind, w)
-        if cells + cost > target_cells * 1.15 and cells >= target_cells * 0.85:
+
+    def cost(kind):
+        if kind in ("dim", "rows"):    # idx*x + t, limit*x, size*x, t < x
+            return w_idx * w + w_lim * w + w_size * w + 4 * w
+        wf = 3 * (w + 1) + w + 2       # width of (N+1)^3 * E * 3
+        return ((w + 1) ** 2 + 2 * (w + 1) ** 2 + (3 * w + 3) * w + 2 * (4 * w + 3)
+                + w_size * wf + w_lim * wf)
+
+    for _ in range(64):
+        kinds = ["dim", "cube", "rows"]
+        first = r.randint(0, 2)
+        choice = None
+        for t in range(3):
+            kd = kinds[(first + t) % 3]
+            if cells + cost(kd) <= budget * 1.15:
+                choice = kd
+                break
+        if choice is None or cells >= budget * 0.85:
             break
-        if cells >= target_cells:
-            break
-        if kind == "dim":
+        cells += cost(choice)
+        if choice == "dim":
             bd = ir.free(w, "bd")
-            t = ir.free(w, "t")
-            ir.assert_(ir.ult(t, bd))
-            idx = ir.add(ir.mul(idx, bd), t)
+            t_ = ir.free(w, "t")
+            ir.assert_(ir.ult(t_, bd))
+            idx = ir.add(ir.mul(idx, bd), t_)
             limit = ir.mul(limit, bd)
             size = ir.mul(size, bd)
-        elif kind == "cube":
+            w_idx, w_lim, w_size = w_idx + w + 1, w_lim + w, w_size + w
+        elif choice == "cube":
             big_n = ir.free(w, "N")
             e = ir.free(w, "E")
             n1 = ir.add(big_n, ir.const(1))
-            cube = ir.mul(ir.mul(n1, n1), n1)
-            f = ir.mul(ir.mul(cube, e), ir.const(3))
+            f = ir.mul(ir.mul(ir.mul(ir.mul(n1, n1), n1), e), ir.const(3))
             size = ir.mul(size, f)
             limit = ir.mul(limit, f)
+            wf = 3 * (w + 1) + w + 2
+            w_lim, w_size = w_lim + wf, w_size + wf
         else:
             rows = ir.free(w, "R")
             col = ir.free(w, "col")
@@ -179,22 +189,22 @@ def grown_query(seed: int, target_cells: int | None = None) -> tuple[IR, dict]:
             idx = ir.add(ir.mul(idx, rows), col)
             limit = ir.mul(limit, rows)
             size = ir.mul(size, rows)
-        structs.append(kind)
-        cells += cost
+            w_idx, w_lim, w_size = w_idx + w + 1, w_lim + w, w_size + w
+        structs.append(choice)
     offset = ir.add(ir.mul(ir.const(a), idx), ir.const(c))
     if use_part:
         m = ir.udiv(size, k)
         p_j = ir.mul(ir.const(j), m)
         end_j = ir.mul(ir.const(j + 1), m) if j < k - 1 else size
         if guard:
-            ir.assert_(ir.ult(idx, ir.udiv(limit, k) if True else limit))
+            ir.assert_(ir.ult(idx, ir.udiv(limit, k)))
         off2 = ir.add(p_j, offset)
         ir.assert_(ir.or_(ir.ult(off2, p_j), ir.ule(end_j, off2)))
     else:
         if guard:
             ir.assert_(ir.ult(idx, limit))
         ir.assert_(ir.ule(size, offset))
-    return ir, dict(w=w, target_cells=target_cells, cells=cells, structs=structs,
+    return ir, dict(w=w, target_clauses=target_clauses, cells=cells, structs=structs,
                     guard=guard, partition=use_part)
 
 
@@ -217,27 +227,37 @@ def random_3sat(seed: int, n_lo: int = 200, n_hi: int = 400, ratio: float = 4.26
     distinct variables per clause, each negated with probability 1/2.
 
     Returns (nvars, lits) with lits an int32 array of shape (m, 3), DIMACS
-    numbering (+-v, v in 1..n)."""
+    numbering (+-v, v in 1..n). Per clause, six candidate variables are drawn
+    and the first three distinct ones are kept (rejection sampling); the rare
+    clause without three distinct candidates redraws from the scalar stream."""
     r = SplitMix64(seed)
     nv = r.randint(n_lo, n_hi)
     m = int(round(ratio * nv))
-    raw = r.u64_block(m * 8).reshape(m, 8)
-    out = np.zeros((m, 3), dtype=np.int32)
-    # three distinct variables: draw with rejection among 6 candidates + fallback
-    for i in range(m):
-        chosen = []
-        t = 0
+    raw = r.u64_block(m * 7).reshape(m, 7)
+    cand = (raw[:, :6] % np.uint64(nv)).astype(np.int64) + 1
+    signs = raw[:, 6]
+    out = np.zeros((m, 3), dtype=np.int64)
+    out[:, 0] = cand[:, 0]
+    # second: first candidate different from the first
+    d1 = cand[:, 1:] != cand[:, :1]
+    has1 = d1.any(axis=1)
+    i1 = np.argmax(d1, axis=1) + 1
+    out[:, 1] = cand[np.arange(m), i1]
+    # third: first candidate after the second's position different from both
+    pos = np.arange(6)[None, :]
+    d2 = (cand != out[:, :1]) & (cand != out[:, 1:2]) & (pos > i1[:, None])
+    has2 = d2.any(axis=1)
+    out[:, 2] = cand[np.arange(m), np.argmax(d2, axis=1)]
+    for i in np.flatnonzero(~(has1 & has2)):
+        chosen = [int(cand[i, 0])]
         while len(chosen) < 3:
-            if t < 6:
-                v = int(raw[i, t] % np.uint64(nv)) + 1
-            else:
-                v = r.randint(1, nv)
-            t += 1
+            v = r.randint(1, nv)
             if v not in chosen:
                 chosen.append(v)
-        signs = int(raw[i, 6])
-        out[i] = [v if (signs >> b) & 1 == 0 else -v for b, v in enumerate(chosen)]
-    return nv, out
+        out[i] = chosen
+    neg = np.stack([(signs >> np.uint64(b)) & np.uint64(1) for b in range(3)], axis=1)
+    out = np.where(neg == 1, -out, out)
+    return nv, out.astype(np.int32)
 
 
 def config4_split(count_train: int = 2048, count_test: int = 4096, w: int = 16):
