@@ -205,6 +205,19 @@ int scuba_solve_batch_host(const scuba_cnf_batch* batch, uint8_t* verdict, uint8
 int scuba_solve_batch_noalloc(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t* model,
                               void* stream, const scuba_options* opt);
 
+/*
+ * Unit-propagation closure (the BCP step of the search, without decisions):
+ * for each instance, assert its unit clauses and the assumption literals
+ * asm_lits[asm_begin[i] .. asm_begin[i+1]) (DEVICE, DIMACS; out-of-range
+ * literals are ignored), propagate to a fixpoint and write values[vb[i] + v]
+ * = 0 open / 1 true / 2 false (DEVICE u8[total_vars]) and conflict[i] = 1
+ * when a clause became false (values then unspecified). The closure is unique
+ * whatever the propagation order. Asynchronous; check with scuba_sync_status.
+ */
+int scuba_propagate_batch(const scuba_cnf_batch* batch, const int64_t* asm_begin,
+                          const int32_t* asm_lits, uint8_t* values, uint8_t* conflict,
+                          void* stream);
+
 /* Waits for `stream` and returns the status of the last solve issued on it. */
 int scuba_sync_status(void* stream);
 

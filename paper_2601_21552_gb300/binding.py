@@ -76,6 +76,7 @@ _sig("scuba_solve_batch_host", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp,
                                       ctypes.POINTER(scuba_options)])
 _sig("scuba_solve_batch_noalloc", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _vp,
                                          ctypes.POINTER(scuba_options)])
+_sig("scuba_propagate_batch", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _vp, _vp, _vp])
 _sig("scuba_sync_status", _i32, [_vp])
 _sig("scuba_release", None, [])
 _sig("scuba_last_error", ctypes.c_char_p, [])
@@ -98,7 +99,7 @@ _sig("scuba_mlp_train", _i32, [ctypes.POINTER(scuba_trace), _i64, _vp, _vp, _vp,
 
 EXPORTED = [
     "scuba_options_init", "scuba_solve_batch", "scuba_solve_batch_ex",
-    "scuba_solve_batch_host", "scuba_solve_batch_noalloc", "scuba_sync_status", "scuba_release", "scuba_last_error",
+    "scuba_solve_batch_host", "scuba_solve_batch_noalloc", "scuba_propagate_batch", "scuba_sync_status", "scuba_release", "scuba_last_error",
     "scuba_version", "scuba_abi_sizes", "scuba_encode_batch", "scuba_encoded_sizes", "scuba_encoded_copy",
     "scuba_encoded_inputs", "scuba_encoded_free", "scuba_encoded_release_clauses",
     "scuba_verify_batch",

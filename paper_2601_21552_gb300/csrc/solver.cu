@@ -1280,6 +1280,81 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? 4 : 5)
   if (counted_idle && lane == 0) atomicSub(&S.ctrl->idle, 1u);
 }
 
+// Unit-propagation closure of each instance under its unit clauses and the
+// caller's assumption literals: one warp per instance, the same BCP as the
+// search. values[vb[i] + v] = 0 open, 1 true, 2 false; conflict[i] = 1 when
+// propagation falsifies a clause (values are then unspecified).
+struct PropArgs {
+  int n;
+  int32_t vmax;
+  uint32_t assign_words;
+  const int64_t* icb;
+  const int64_t* cb;
+  const int32_t* lits;
+  const int32_t* nv;
+  const int64_t* vb;
+  const int64_t* occ_base;
+  const uint32_t* occ_begin;
+  const uint64_t* ent;
+  const uint32_t* units;
+  const uint32_t* nunits;
+  const uint32_t* flags;
+  const int64_t* asm_begin;   // [n+1]
+  const int32_t* asm_lits;    // DIMACS
+  uint32_t* trail;            // [slots][vmax]
+  uint8_t* values;
+  uint8_t* conflict;
+  Ctrl* ctrl;
+};
+
+__global__ void __launch_bounds__(256) k_propagate(const __grid_constant__ PropArgs A) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  WarpShared* wsh = reinterpret_cast<WarpShared*>(smem);
+  Warp w;
+  w.S = nullptr;
+  w.ws = &wsh[wib];
+  w.asg = smem + (sizeof(WarpShared) / 4) * wpb + (size_t)A.assign_words * wib;
+  w.lane = lane;
+  const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
+  w.trail = A.trail + slot * A.vmax;
+  if (batch_failed(A.ctrl)) return;
+  for (int i = (int)(blockIdx.x * wpb + wib); i < A.n; i += gridDim.x * wpb) {
+    if (A.flags[i] & F_BAD) continue;
+    w.V = (uint32_t)A.nv[i];
+    w.c0 = A.icb[i];
+    w.occ = A.occ_begin + A.occ_base[i];
+    const int64_t lbase = A.icb[i] < A.icb[i + 1] ? A.cb[A.icb[i]] : 0;
+    w.ent = A.ent + lbase;
+    w.head = 0;
+    const uint32_t nwords = (w.V + 15u) >> 4;
+    for (uint32_t k = lane; k < nwords; k += 32) w.asg[k] = 0u;
+    if (lane == 0) {
+      w.ws->tail = 0;
+      w.ws->conflict = 0;
+      w.ws->props = w.ws->visits = 0;
+    }
+    __syncwarp();
+    bool confl = (A.flags[i] & F_EMPTY) != 0;
+    for (uint32_t k = lane; k < A.nunits[i] && !confl; k += 32)
+      if (!imply(w, A.units[w.c0 + k])) record_conflict(w, 0, NONE, NONE);
+    for (int64_t k = A.asm_begin[i] + lane; k < A.asm_begin[i + 1]; k += 32) {
+      const int32_t l = A.asm_lits[k];
+      if (l == 0 || l > (int32_t)w.V || l < -(int32_t)w.V) continue;
+      if (!imply(w, code_of(l))) record_conflict(w, 0, NONE, NONE);
+    }
+    __syncwarp();
+    confl = confl || w.ws->conflict != 0;
+    if (!confl) confl = bcp(w);
+    if (lane == 0) A.conflict[i] = confl ? 1 : 0;
+    for (uint32_t x = lane; x < w.V; x += 32) {
+      const uint32_t bits = (w.asg[x >> 4] >> ((x & 15u) * 2u)) & 3u;
+      A.values[A.vb[i] + x] = (uint8_t)(bits == 3u ? 0u : bits);
+    }
+    __syncwarp();
+  }
+}
+
 // Instances still open when the kernel stopped (timeout / abort) -> UNKNOWN.
 __global__ void k_finalize(Solve S) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
@@ -1335,6 +1410,7 @@ struct Scratch {
   int sms = 0;
   int32_t last_status = 0;
   int smem_set[3] = {0, 0, 0};  // dynamic shared memory granted per search mode
+  int smem_prop = 0;
 };
 
 std::map<int, Scratch>& scratch_map() {
@@ -1925,4 +2001,109 @@ extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verd
   if (e != cudaSuccess) return cuda_fail("cudaMemcpy", e);
   if (status != 0) set_error("scuba_solve_batch_noalloc: device status " + std::to_string(status));
   return status;
+}
+
+extern "C" int scuba_propagate_batch(const scuba_cnf_batch* b, const int64_t* asm_begin,
+                                     const int32_t* asm_lits, uint8_t* values,
+                                     uint8_t* conflict, void* stream) {
+  using namespace scuba;
+  if (!b || b->num_instances < 0 || b->max_vars < 0 || b->total_vars < 0 ||
+      b->total_clauses < 0 || b->total_lits < 0) {
+    set_error("scuba_propagate_batch: bad arguments");
+    return SCUBA_ERR_ARG;
+  }
+  const int n = b->num_instances;
+  if (n == 0) return SCUBA_OK;
+  if (!asm_begin || !values || !conflict || !b->inst_clause_begin || !b->clause_begin ||
+      !b->inst_num_vars || !b->inst_var_begin || (b->total_lits > 0 && !b->lits)) {
+    set_error("scuba_propagate_batch: NULL array");
+    return SCUBA_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+  Scratch& S = scratch_map()[dev];
+  if (!S.sms) {
+    e = cudaDeviceGetAttribute(&S.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceGetAttribute", e);
+  }
+  const int64_t C = b->total_clauses, L = b->total_lits;
+  const int vmax = std::max(1, (int)b->max_vars);
+  const int64_t occ_total = 2LL * b->total_vars + n;
+  const int wpb = 8;
+  const uint32_t assign_words = (uint32_t)((vmax + 15) / 16);
+  const size_t smem = (sizeof(dev::WarpShared) + (size_t)assign_words * 4) * wpb;
+  if (smem > 227 * 1024) return SCUBA_ERR_TOO_LARGE;
+  const int blocks = S.sms;
+  const int64_t slots = (int64_t)blocks * wpb;
+  if (ensure(S.occ_base, 8 * (size_t)(n + 1)) || ensure(S.norm, 4 * (size_t)L) ||
+      ensure(S.occ_cnt, 4 * (size_t)occ_total) || ensure(S.occ_begin, 4 * (size_t)occ_total) ||
+      ensure(S.ent, 8 * (size_t)L) || ensure(S.units, 4 * (size_t)std::max<int64_t>(C, 1)) ||
+      ensure(S.nunits, 4 * (size_t)n) || ensure(S.flags, 4 * (size_t)n) ||
+      ensure(S.trail, 4 * (size_t)slots * vmax) || ensure(S.ctrl, sizeof(dev::Ctrl)))
+    return SCUBA_ERR_NOMEM;
+  dev::Prep pr;
+  pr.n = n;
+  pr.C = C;
+  pr.L = L;
+  pr.icb = b->inst_clause_begin;
+  pr.cb = b->clause_begin;
+  pr.lits = b->lits;
+  pr.nv = b->inst_num_vars;
+  pr.occ_base = P<int64_t>(S.occ_base);
+  pr.norm = P<uint32_t>(S.norm);
+  pr.occ_cnt = P<uint32_t>(S.occ_cnt);
+  pr.occ_begin = P<uint32_t>(S.occ_begin);
+  pr.ent = P<uint64_t>(S.ent);
+  pr.units = P<uint32_t>(S.units);
+  pr.nunits = P<uint32_t>(S.nunits);
+  pr.flags = P<uint32_t>(S.flags);
+  pr.total_vars = b->total_vars;
+  pr.occ_cap = occ_total;
+  pr.vmax = vmax;
+  pr.vb = b->inst_var_begin;
+  pr.ctrl = P<dev::Ctrl>(S.ctrl);
+  dev::k_init_ctrl<<<1, 1, 0, st>>>(pr.ctrl, (uint32_t)n);
+  cudaMemsetAsync(pr.occ_cnt, 0, 4 * (size_t)occ_total, st);
+  cudaMemsetAsync(pr.flags, 0, 4 * (size_t)n, st);
+  dev::k_occ_base<<<1, 1024, 0, st>>>(pr);
+  if (C > 0) {
+    int grid = (int)std::min<int64_t>((C + 255) / 256, (int64_t)S.sms * 32);
+    dev::k_normalize<<<grid, 256, 0, st>>>(pr);
+  }
+  int wgrid = (int)std::min<int64_t>((n + 7) / 8, (int64_t)S.sms * 16);
+  dev::k_occ_scan<<<wgrid, 256, 0, st>>>(pr);
+  dev::k_fill<<<wgrid, 256, 0, st>>>(pr);
+  dev::PropArgs A;
+  A.n = n;
+  A.vmax = vmax;
+  A.assign_words = assign_words;
+  A.icb = b->inst_clause_begin;
+  A.cb = b->clause_begin;
+  A.lits = b->lits;
+  A.nv = b->inst_num_vars;
+  A.vb = b->inst_var_begin;
+  A.occ_base = pr.occ_base;
+  A.occ_begin = pr.occ_begin;
+  A.ent = pr.ent;
+  A.units = pr.units;
+  A.nunits = pr.nunits;
+  A.flags = pr.flags;
+  A.asm_begin = asm_begin;
+  A.asm_lits = asm_lits;
+  A.trail = P<uint32_t>(S.trail);
+  A.values = values;
+  A.conflict = conflict;
+  A.ctrl = pr.ctrl;
+  if ((int)smem > S.smem_prop) {
+    e = cudaFuncSetAttribute(dev::k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
+    S.smem_prop = (int)smem;
+  }
+  dev::k_propagate<<<blocks, 32 * wpb, smem, st>>>(A);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("kernel launch", e);
+  return SCUBA_OK;
 }
