@@ -436,6 +436,8 @@ struct Warp {
   uint32_t V;
   const uint32_t* occ;
   const uint64_t* ent;
+  const int64_t* cb;       // the caller's clause_begin (long clauses)
+  const int32_t* lits;     // the caller's literals (long clauses)
   int64_t c0;
   uint32_t head;
   uint32_t nd;
@@ -479,11 +481,11 @@ __device__ __forceinline__ bool imply(Warp& w, uint32_t l) {
 
 __device__ void eval_long(Warp& w, uint32_t local, uint32_t f) {
   const int64_t c = w.c0 + local;
-  const int64_t b = w.S->cb[c], e = w.S->cb[c + 1];
+  const int64_t b = w.cb[c], e = w.cb[c + 1];
   uint32_t open_lit = NONE;
   int n_open = 0;
   for (int64_t q = b; q < e; q++) {
-    uint32_t x = code_of(__ldg(&w.S->lits[q]));
+    uint32_t x = code_of(__ldg(&w.lits[q]));
     uint32_t vx = lit_value(w.asg, x);
     if (vx == LV_T || vx == LV_X) return;
     if (vx == LV_U && x != open_lit) {
@@ -612,7 +614,7 @@ __device__ void bump(Warp& w) {
       uint32_t* cnt = w.lvlcnt + (size_t)w.lane * w.S->vmax;
       if (a & LONG_CLAUSE) {
         const int64_t cl = w.c0 + (a & ~LONG_CLAUSE);
-        for (int64_t q = w.S->cb[cl]; q < w.S->cb[cl + 1]; q++) cnt[code_of(w.S->lits[q]) >> 1]++;
+        for (int64_t q = w.cb[cl]; q < w.cb[cl + 1]; q++) cnt[code_of(w.lits[q]) >> 1]++;
       } else {
         if (a != NONE) cnt[a >> 1]++;
         if (b != NONE) cnt[b >> 1]++;
@@ -625,8 +627,8 @@ __device__ void bump(Warp& w) {
   if (w.lane == 0) {
     if (a & LONG_CLAUSE) {
       const int64_t cl = w.c0 + (a & ~LONG_CLAUSE);
-      for (int64_t q = w.S->cb[cl]; q < w.S->cb[cl + 1]; q++) {
-        uint32_t v = code_of(w.S->lits[q]) >> 1;
+      for (int64_t q = w.cb[cl]; q < w.cb[cl + 1]; q++) {
+        uint32_t v = code_of(w.lits[q]) >> 1;
         w.act[v] += w.inc;
         big |= w.act[v] > 1e20f;
       }
@@ -1179,6 +1181,8 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? 4 : 5)
                 : S.trail + slot * S.vmax;
   w.dstack = S.dstack + slot * S.vmax;
   w.act = S.act + slot * S.vmax;
+  w.cb = S.cb;
+  w.lits = S.lits;
   w.lane = lane;
   w.lvlcnt = nullptr;
   w.lvl_node = nullptr;
@@ -1312,7 +1316,9 @@ __global__ void __launch_bounds__(256) k_propagate(const __grid_constant__ PropA
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   WarpShared* wsh = reinterpret_cast<WarpShared*>(smem);
   Warp w;
-  w.S = nullptr;
+  w.S = nullptr;  // the propagate kernel has no search state; BCP reads only w.*
+  w.cb = A.cb;
+  w.lits = A.lits;
   w.ws = &wsh[wib];
   w.asg = smem + (sizeof(WarpShared) / 4) * wpb + (size_t)A.assign_words * wib;
   w.lane = lane;
