@@ -49,8 +49,7 @@ def cpu_closure(nv, clauses, assumptions):
         sat = (lv == 1).any(axis=1)
         opn = (lv == 0)
         # distinct open literals per clause
-        ol = np.where(opn, C, 0)
-        first = ol.max(axis=1)
+        first = np.where(opn, C, np.iinfo(np.int64).min).max(axis=1)
         lo = np.where(opn, C, np.iinfo(np.int64).max).min(axis=1)
         nopen = opn.sum(axis=1)
         single = (nopen >= 1) & (first == lo)
