@@ -270,6 +270,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(dev)  # graphs cannot be captured on the legacy stream
 
+    from paper_2601_21552_gb300 import autotune
+    tuned = autotune.load()  # launch shape / sharing parameters from the last sweep
     arms = ["plain", "learned"] if args.heuristic == "both" else [args.heuristic]
     net, train_info = None, None
     if "learned" in arms:
@@ -280,9 +282,9 @@ def run_ours(args):
     results = {}
     with ClockSampler(local) as clk:
         for arm in arms:
-            opts = {}
+            opts = dict(tuned)
             if arm == "learned":
-                opts = dict(heuristic=B.SCUBA_HEUR_LEARNED, mlp_weights=net.weights,
+                opts.update(heuristic=B.SCUBA_HEUR_LEARNED, mlp_weights=net.weights,
                             learned_depth=args.learned_depth)
             results[arm] = _timed_arm(api, B, db, dev, stream, count, opts, args,
                                       use_graph=args.graph)
@@ -358,7 +360,8 @@ def run_ours(args):
                    "clauses_total": enc.total_clauses, "literals_total": enc.total_lits,
                    "vars_total": enc.total_vars,
                    "l2": "inputs larger than L2 (CSR + occurrence lists > 1 GB)",
-                   "encode_s": t_enc, "cuda_graph": args.graph, "parity": parity},
+                   "encode_s": t_enc, "cuda_graph": args.graph, "parity": parity,
+                   "autotuned": tuned},
         "arms": summ,
         "e2e": {"value": count / float(np.median(e2e_t)), "unit": "verdicts/s",
                 "h2d_bytes_per_step": db.h2d_bytes, "d2h_bytes_per_step": count},

@@ -158,6 +158,10 @@ def solve(db: DeviceBatch, want_model: bool = True, stats: bool = True,
     stats i64[n,3] | None) device tensors. Asynchronous: call
     ``status(stream)`` to wait and collect the device status."""
     dev = db.icb.device
+    if opts.pop("tuned", False):
+        from . import autotune
+        for k, v in autotune.load().items():
+            opts.setdefault(k, v)
     if opts.get("order") == "lpt":
         opts["order"] = db.lpt_order()
     verdict = torch.empty(max(db.n, 1), dtype=torch.uint8, device=dev)
