@@ -48,7 +48,6 @@ struct Builder {
   int nvars = 0;
   std::vector<int64_t> cb{0};
   std::vector<int32_t> lits;
-  std::unordered_map<uint64_t, int> memo;  // structural hashing of gates
 
   int fresh() { return ++nvars; }
   void clause(std::initializer_list<int> ls) {
@@ -176,7 +175,6 @@ Word mul(Builder& B, const Word& a, const Word& b) {
   Word out(W, kFalse);
   for (size_t c = 0; c < W; c++) {
     auto& v = col[c];
-    // fold constant TRUE bits pairwise into carries is handled by the gadgets
     size_t head = 0;
     while (v.size() - head > 1) {
       if (v.size() - head >= 3) {
@@ -279,8 +277,6 @@ struct Encoder {
     return divs[key] = {q, r};
   }
 
-  int get_bool(int64_t i) { return boolean[i]; }
-
   int run(const int64_t* roots, int64_t r, std::vector<int32_t>& in_map,
           std::vector<int32_t>& widths) {
     word.assign(n, Word());
@@ -297,9 +293,9 @@ struct Encoder {
       widths.push_back(w);
       for (int k = 0; k < w; k++) in_map.push_back(v[k]);
     }
-    // asserted roots that are positive equalities or conjunctions are
-    // emitted directly; everything else is built as a circuit on demand
-    std::vector<char> direct(n, 0);
+    // asserted conjunctions are split and positive equalities are emitted
+    // as bitwise equivalences; every other asserted node becomes a unit clause
+    // on the output of its circuit
     std::vector<std::pair<int64_t, bool>> todo;
     for (int64_t k = 0; k < r; k++) todo.push_back({roots[k], true});
     std::vector<std::pair<int64_t, bool>> asserted;
@@ -324,7 +320,6 @@ struct Encoder {
         B.assert_lit(pol ? b : -b);
       }
     }
-    (void)direct;
     return 0;
   }
 
@@ -347,9 +342,8 @@ struct Encoder {
   }
 };
 
-// Equality circuits are only built for EQ nodes that are used under OR/NOT;
-// an EQ that is only asserted positively keeps boolean[i] unused, which costs
-// a few dead gates. Keep it simple: build() always builds them.
+// build() constructs every node's circuit, including equality circuits of EQ
+// nodes that are only asserted positively (a few dead, definitional gates).
 
 int validate(const int64_t* a, int64_t len) {
   if (!a || len < 4 || a[0] != kMagic || a[1] != kVersion) return -1;

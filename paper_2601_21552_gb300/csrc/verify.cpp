@@ -73,9 +73,8 @@ Big mul(const Big& a, const Big& b) {
   return r;
 }
 
-// a / k and a % k for a 62-bit constant k >= 1 (long division, 16-bit digits
-// so every partial remainder fits in 64 bits... k < 2^62 needs care: use
-// bitwise long division, which is plain and exact)
+// a / k and a % k for a constant 1 <= k < 2^62 by bitwise long division (the
+// partial remainder stays below 2k < 2^63 and is kept in 128 bits anyway)
 void divmod(const Big& a, uint64_t k, Big& q, Big& r) {
   size_t nbits = a.size() * 32;
   q.assign(a.size(), 0);
