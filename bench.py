@@ -37,6 +37,24 @@ METRIC = "verdicts/sec + BCP propagations/sec on 1 GB300, learned vs plain, bit-
 WORKLOAD = "partition queries, 16-bit inputs (4,096 per GPU)"
 
 
+# DRAM traffic of the plain search kernel from one ncu capture (the 1,024-query
+# case of profiles/k_solve_partition16_1024.md: 0.744 GB for 1.05e9
+# propagations), per propagation, valid only for the kernel sources it was
+# taken on (sha256 prefix of solver.cu + learn.cuh); scaled to a full launch
+# by the propagations it processes.
+PROFILED_SOURCES = "dcbcae6f9b12e8c3"
+DRAM_BYTES_PER_PROPAGATION = 0.744e9 / (3.9957e9 * 0.2626)
+
+
+def _kernel_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("solver.cu", "learn.cuh"):
+        with open(os.path.join(ROOT, "paper_2601_21552_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -367,8 +385,12 @@ def run_ours(args):
                 "h2d_bytes_per_step": db.h2d_bytes, "d2h_bytes_per_step": count},
         "gpu_launches": 10 * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "k_solve",
-                     "peak_source": src, "search_ms": head["search_ms"]},
+                     "frac": achieved / hbm,
+                     "traffic": (DRAM_BYTES_PER_PROPAGATION * head["propagations_per_s"]
+                                 * head["ms_per_step"] * 1e-3 / ws
+                                 if _kernel_sources_sha() == PROFILED_SOURCES else None),
+                     "traffic_unit": "bytes per launch (ncu, scaled by propagations)",
+                     "kernel": "k_solve", "peak_source": src, "search_ms": head["search_ms"]},
         "clocks": clk.summary(),
     }
     if train_info:
