@@ -43,6 +43,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    defs = []
+    if os.environ.get("SCUBA_LEARNED_MINBLOCKS"):
+        defs.append("-DSCUBA_LEARNED_MINBLOCKS=" + str(int(os.environ["SCUBA_LEARNED_MINBLOCKS"])))
     jobs = []
     objs = []
     for s in HOST_SRCS:
@@ -55,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         jobs.append([_nvcc(), "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, s), "-o", o]
-                    + ARCH + inc)
+                    + ARCH + inc + defs)
 
     def run(cmd):
         if verbose:

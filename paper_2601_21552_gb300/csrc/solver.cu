@@ -657,7 +657,8 @@ __device__ void bump(Warp& w) {
 // For variable v (0-based) and each polarity: how many clauses containing the
 // literal are not yet satisfied with 2 / 3 open literals, its static
 // occurrence count, plus activity, input-bit flags and search progress.
-__device__ void var_features(const Warp& w, uint32_t v, uint32_t ninputs, float f[16]) {
+template <class Out>
+__device__ void var_features(const Warp& w, uint32_t v, uint32_t ninputs, Out&& put) {
   uint32_t c2[2] = {0, 0}, c3[2] = {0, 0}, occn[2];
 #pragma unroll
   for (int pol = 0; pol < 2; pol++) {
@@ -681,22 +682,22 @@ __device__ void var_features(const Warp& w, uint32_t v, uint32_t ninputs, float 
     }
   }
   const float tail = (float)*(volatile uint32_t*)&w.ws->tail;
-  f[0] = c2[0] * 0.25f;
-  f[1] = c3[0] * 0.25f;
-  f[2] = c2[1] * 0.25f;
-  f[3] = c3[1] * 0.25f;
-  f[4] = occn[0] * 0.125f;
-  f[5] = occn[1] * 0.125f;
-  f[6] = fminf(w.act[v] / w.inc, 16.0f) * 0.0625f;
-  f[7] = v < ninputs ? 1.0f : 0.0f;
-  f[8] = v < ninputs ? (float)v / (float)ninputs : 0.0f;
-  f[9] = (float)w.nd * (1.0f / 32.0f);
-  f[10] = w.V ? tail / (float)w.V : 0.0f;
-  f[11] = (c2[0] + c2[1]) * 0.125f;
-  f[12] = (c3[0] + c3[1]) * 0.125f;
-  f[13] = log2f(1.0f + occn[0] + occn[1]) * (1.0f / 6.0f);
-  f[14] = ((float)(c2[0] + c3[0]) - (float)(c2[1] + c3[1])) * 0.125f;
-  f[15] = 1.0f;
+  put(0, c2[0] * 0.25f);
+  put(1, c3[0] * 0.25f);
+  put(2, c2[1] * 0.25f);
+  put(3, c3[1] * 0.25f);
+  put(4, occn[0] * 0.125f);
+  put(5, occn[1] * 0.125f);
+  put(6, fminf(w.act[v] / w.inc, 16.0f) * 0.0625f);
+  put(7, v < ninputs ? 1.0f : 0.0f);
+  put(8, v < ninputs ? (float)v / (float)ninputs : 0.0f);
+  put(9, (float)w.nd * (1.0f / 32.0f));
+  put(10, w.V ? tail / (float)w.V : 0.0f);
+  put(11, (c2[0] + c2[1]) * 0.125f);
+  put(12, (c3[0] + c3[1]) * 0.125f);
+  put(13, log2f(1.0f + occn[0] + occn[1]) * (1.0f / 6.0f));
+  put(14, ((float)(c2[0] + c3[0]) - (float)(c2[1] + c3[1])) * 0.125f);
+  put(15, 1.0f);
 }
 
 __device__ __forceinline__ bool var_unassigned(const uint32_t* asg, uint32_t v) {
@@ -737,11 +738,8 @@ __device__ void trace_open(Warp& w, uint32_t depth) {
     const uint32_t m = __ballot_sync(FULL, un);
     if (un) {
       const long long row = r + __popc(m & ((1u << w.lane) - 1u));
-      float f[16];
-      var_features(w, v, ni, f);
       __nv_bfloat16* xr = T.x + row * learn::NFEAT;
-#pragma unroll
-      for (int k = 0; k < 16; k++) xr[k] = __float2bfloat16(f[k]);
+      var_features(w, v, ni, [&](int k, float x) { xr[k] = __float2bfloat16(x); });
       T.var[row] = (int32_t)v;
       T.target[row] = 0.0f;
     }
@@ -779,13 +777,13 @@ __device__ uint32_t pick_learned(Warp& w) {
     const uint32_t v = base + w.lane;
     const bool un = v < w.V && var_unassigned(w.asg, v);
     if (!__any_sync(FULL, un)) continue;
-    float f[16];
-    if (un) var_features(w, v, ni, f);
-    else
-      for (int k = 0; k < 16; k++) f[k] = 0.0f;
     __nv_bfloat16* xr = w.xtile + w.lane * learn::NFEAT;
+    if (un) {
+      var_features(w, v, ni, [&](int k, float x) { xr[k] = __float2bfloat16(x); });
+    } else {
 #pragma unroll
-    for (int k = 0; k < 16; k++) xr[k] = __float2bfloat16(f[k]);
+      for (int k = 0; k < 16; k++) xr[k] = __float2bfloat16(0.0f);
+    }
     __syncwarp();
     float a_lo, a_hi, b_lo, b_hi;
     learn::mlp_tile_scores(S.mlp, w.xtile, w.lane, a_lo, a_hi);
@@ -1161,9 +1159,14 @@ __device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* j
 }
 
 // Plain search: 48 registers per thread, 5 blocks x 8 warps = 40 resident
-// warps per SM. The learned variant (MLP on the tensor cores) gets 64.
+// warps per SM. The learned variant (MLP on the tensor cores) defaults to 4
+// blocks (64 registers); SCUBA_LEARNED_MINBLOCKS=5 trades spills for warps
+// (measured slower).
+#ifndef SCUBA_LEARNED_MINBLOCKS
+#define SCUBA_LEARNED_MINBLOCKS 4
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? 4 : 5)
+__global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINBLOCKS : 5)
     k_solve(const __grid_constant__ Solve S) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31;
@@ -1560,7 +1563,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
     return SCUBA_ERR_TOO_LARGE;
   }
   while (bps > 1 && (smem + 1024) * bps > sm_cap) bps--;
-  if (mode == dev::MODE_LEARNED) bps = std::min(bps, 4);
+  if (mode == dev::MODE_LEARNED) bps = std::min(bps, SCUBA_LEARNED_MINBLOCKS);
   const int64_t slots = (int64_t)S.sms * bps * wpb;
   const uint32_t ring_cap = 2048;
 
