@@ -120,6 +120,26 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank timing over all ranks (identity without a process
+    group); the backend is whatever torch.distributed was initialised with."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(count_per_rank: int, world_size: int, ms_per_step: float) -> float:
+    """Whole-job verdicts/s: every rank solves its own batch of
+    count_per_rank queries per step (weak scaling), the step time is the max
+    over ranks."""
+    return count_per_rank * world_size / (ms_per_step * 1e-3)
+
+
 def _workload(rank: int, count: int, width: int = 16):
     from workloads import queries
     seed0 = queries.SEED_BASE[2] + rank * 1_000_000
@@ -312,10 +332,8 @@ def run_ours(args):
                                       use_graph=args.graph)
     if ws > 1:
         torch.distributed.barrier()
-        for arm in arms:
-            t = torch.tensor([results[arm]["ms_total"]], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            results[arm]["ms_total"] = float(t.item())
+    for arm in arms:
+        results[arm]["ms_total"] = max_over_ranks(results[arm]["ms_total"], dev)
 
     # parity after timing: both arms bit-exact against the stored oracle verdicts
     parity = {}
@@ -354,7 +372,7 @@ def run_ours(args):
         props = st[:, 2].sum()
         alg_bytes = 16 * props + 8 * st[:, 3].sum() + 4 * st[:, 4].sum() + 4 * st[:, 5].sum()
         search_ms = float(np.mean(r["ms_search"]))
-        return {"value": count * ws / (ms_step * 1e-3), "unit": "verdicts/s",
+        return {"value": aggregate_value(count, ws, ms_step), "unit": "verdicts/s",
                 "ms_per_step": ms_step, "propagations_per_s": props * ws / (ms_step * 1e-3),
                 "decisions_per_step": float(st[:, 0].sum()),
                 "search_ms": search_ms, "search_ms_steps": r["ms_search"],
