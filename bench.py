@@ -220,7 +220,7 @@ def _train_network(api, B, dev, args):
     tr_irs, _, _, _ = queries.config4_split(args.train_queries, 0, w=args.width)
     enc = B.scuba_encode_batch(tr_irs)
     db = api.DeviceBatch(enc, dev)
-    trace, _, _ = api.record_trace(db, depth=args.learned_depth, max_nodes=1 << 17,
+    trace, _, _ = api.record_trace(db, depth=args.trace_depth, max_nodes=1 << 17,
                                    max_rows=1 << 25, decision_budget=args.trace_budget,
                                    time_budget_ms=300000)
     nodes, rows = trace.used()
@@ -231,7 +231,8 @@ def _train_network(api, B, dev, args):
     info = {"train_queries": args.train_queries, "trace_nodes": nodes, "trace_rows": rows,
             "epochs": args.epochs, "loss_first": losses[0] if losses else None,
             "loss_last": losses[-1] if losses else None,
-            "train_s": time.perf_counter() - t0, "learned_depth": args.learned_depth}
+            "train_s": time.perf_counter() - t0, "learned_depth": args.learned_depth,
+            "trace_depth": args.trace_depth}
     del trace
     return net, info
 
@@ -435,7 +436,10 @@ def main():
     ap.add_argument("--heuristic", default="both", choices=["plain", "learned", "both"])
     ap.add_argument("--graph", action="store_true",
                     help="replay each step from a captured CUDA graph")
-    ap.add_argument("--learned-depth", type=int, default=6)
+    ap.add_argument("--learned-depth", type=int, default=6,
+                    help="decisions at depth < this are scored by the network")
+    ap.add_argument("--trace-depth", type=int, default=8,
+                    help="decisions at depth < this are recorded for training")
     ap.add_argument("--train-queries", type=int, default=2048)
     ap.add_argument("--trace-budget", type=int, default=20000,
                     help="decision budget per training query while tracing")
