@@ -14,12 +14,16 @@ What each function follows in the paper:
   DPLL (unit propagation, activity decisions, chronological backtracking).
 * ``brute_force`` -- the definition itself (Sec. IV-A: "under any possible
   input"): enumerate every input and evaluate the constraints exactly.
-* ``rup_check`` -- independent checker for the DPLL's refutation trace.
+* ``cdcl`` -- the same decision by plain conflict-driven clause learning
+  (first-UIP clauses, backjumping, restarts; cdcl.c). The paper's solver
+  learns internally without further detail; this is the textbook loop.
+* ``rup_check`` -- independent checker for the refutation traces of both.
 
 Parity status: encode+dpll are pinned by brute force (widths <= 6), by
 closed forms (bounds and partition families at 8 and 16 bits), by the
 paper's worked examples (tests/golden), by model re-verification and by the
-RUP checker. No function here is unpinned.
+RUP checker; cdcl by the RUP check of its learned clauses, model checks,
+brute force and the same corpora. No function here is unpinned.
 """
 from __future__ import annotations
 
@@ -55,9 +59,11 @@ def lib():
         L.oracle_brute_force.restype = i32
         L.oracle_brute_force.argtypes = [P, i64, i32, P]
         L.oracle_solve_queries.restype = None
-        L.oracle_solve_queries.argtypes = [i32, P, P, i32, i64, P, P, P, i32, P]
+        L.oracle_solve_queries.argtypes = [i32, P, P, i32, i64, P, P, P, i32, P, i32]
         L.oracle_solve_cnfs.restype = None
-        L.oracle_solve_cnfs.argtypes = [i32, P, P, P, P, P, i32, i64, P, P]
+        L.oracle_solve_cnfs.argtypes = [i32, P, P, P, P, P, i32, i64, P, P, i32]
+        L.oracle_cdcl.restype = i32
+        L.oracle_cdcl.argtypes = [i32, i64, P, P, i64, P, P, P, i64, P]
         L.rup_check.restype = i32
         L.rup_check.argtypes = [i32, i64, P, P, i64, P]
         _lib = L
@@ -106,17 +112,14 @@ def encode(ir_array: np.ndarray) -> CNF:
         lib().oracle_cnf_free(h)
 
 
-def dpll(cnf: CNF, budget: int = 1 << 40, want_trace: bool = False, trace_cap: int = 1 << 24):
-    """Solve one CNF. Returns dict(verdict, model, decisions, conflicts,
-    propagations, trace)."""
+def _solve_one(fn, cnf: CNF, budget: int, want_trace: bool, trace_cap: int):
     model = np.zeros(max(cnf.nvars, 1), dtype=np.uint8)
     stats = np.zeros(3, dtype=np.int64)
     tl = np.zeros(1, dtype=np.int64)
     tbuf = np.zeros(trace_cap if want_trace else 1, dtype=np.int32)
-    v = lib().oracle_dpll(cnf.nvars, cnf.nclauses, _p(cnf.clause_begin), _p(cnf.lits),
-                          int(budget), _p(model), _p(stats),
-                          _p(tbuf) if want_trace else None, trace_cap if want_trace else 0,
-                          _p(tl))
+    v = fn(cnf.nvars, cnf.nclauses, _p(cnf.clause_begin), _p(cnf.lits), int(budget),
+           _p(model), _p(stats), _p(tbuf) if want_trace else None,
+           trace_cap if want_trace else 0, _p(tl))
     trace = None
     if want_trace:
         if tl[0] < 0:
@@ -124,6 +127,20 @@ def dpll(cnf: CNF, budget: int = 1 << 40, want_trace: bool = False, trace_cap: i
         trace = tbuf[:tl[0]].copy()
     return dict(verdict=int(v), model=model[:cnf.nvars].copy(), decisions=int(stats[0]),
                 conflicts=int(stats[1]), propagations=int(stats[2]), trace=trace)
+
+
+def dpll(cnf: CNF, budget: int = 1 << 40, want_trace: bool = False, trace_cap: int = 1 << 24):
+    """Solve one CNF by plain DPLL. Returns dict(verdict, model, decisions,
+    conflicts, propagations, trace); the budget counts decisions and the trace
+    holds NOT(decisions) of every refuted node, then the empty clause."""
+    return _solve_one(lib().oracle_dpll, cnf, budget, want_trace, trace_cap)
+
+
+def cdcl(cnf: CNF, budget: int = 1 << 40, want_trace: bool = False, trace_cap: int = 1 << 24):
+    """Solve one CNF by plain CDCL (first-UIP learning, backjumping, restarts).
+    Same result dict as dpll; the budget counts conflicts and the trace holds
+    every learned clause, then the empty clause on UNSAT."""
+    return _solve_one(lib().oracle_cdcl, cnf, budget, want_trace, trace_cap)
 
 
 def rup_check(cnf: CNF, trace: np.ndarray) -> int:
@@ -146,9 +163,13 @@ def default_threads() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1
 
 
+ALGOS = {"dpll": 0, "cdcl": 1}
+
+
 def solve_queries(irs: list[np.ndarray], threads: int | None = None, budget: int = 1 << 40,
-                  max_words: int = 64):
-    """Encode and solve many queries on a thread pool. Returns dict with
+                  max_words: int = 64, algo: str = "dpll"):
+    """Encode and solve many queries on a thread pool (algo "dpll" or "cdcl";
+    the budget counts decisions, resp. conflicts). Returns dict with
     verdict[n], stats[n,3] (decisions, conflicts, propagations), words[n,
     max_words] (input words of each SAT model, FREE-node order) and
     size[n,2] (vars, clauses of the oracle's own CNF)."""
@@ -163,11 +184,12 @@ def solve_queries(irs: list[np.ndarray], threads: int | None = None, budget: int
     size = np.zeros((max(n, 1), 2), dtype=np.int64)
     lib().oracle_solve_queries(n, _p(buf), _p(offs), int(threads or default_threads()),
                                int(budget), _p(verdict), _p(stats), _p(words), max_words,
-                               _p(size))
+                               _p(size), ALGOS[algo])
     return dict(verdict=verdict[:n], stats=stats[:n], words=words[:n], size=size[:n])
 
 
-def solve_cnfs(cnfs: list[CNF], threads: int | None = None, budget: int = 1 << 40):
+def solve_cnfs(cnfs: list[CNF], threads: int | None = None, budget: int = 1 << 40,
+               algo: str = "dpll"):
     n = len(cnfs)
     nv = np.array([c.nvars for c in cnfs] or [0], dtype=np.int32)
     cb_off = np.zeros(n + 1, dtype=np.int64)
@@ -184,5 +206,5 @@ def solve_cnfs(cnfs: list[CNF], threads: int | None = None, budget: int = 1 << 4
     stats = np.zeros((max(n, 1), 3), dtype=np.int64)
     lib().oracle_solve_cnfs(n, _p(nv), _p(cb_off), _p(cb), _p(lit_off), _p(lits),
                             int(threads or default_threads()), int(budget), _p(verdict),
-                            _p(stats))
+                            _p(stats), ALGOS[algo])
     return dict(verdict=verdict[:n], stats=stats[:n])

@@ -11,7 +11,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
-SOURCES = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "rup.c")]
+SOURCES = [os.path.join(HERE, "oracle.c"), os.path.join(HERE, "cdcl.c"),
+           os.path.join(HERE, "rup.c")]
 
 
 def build(force: bool = False) -> str:

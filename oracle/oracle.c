@@ -665,9 +665,20 @@ typedef struct {
   uint64_t *words;     /* query mode: per query, up to words_stride input words */
   int words_stride;
   int64_t *cnf_size;   /* query mode: n x 2 (vars, clauses) */
+  int algo;            /* 0 DPLL, 1 CDCL (cdcl.c; the budget then counts conflicts) */
   int next;
   pthread_mutex_t mu;
 } batch_t;
+
+int oracle_cdcl(int nv, int64_t nc, const int64_t *cb, const int32_t *lits,
+                int64_t budget, uint8_t *model, int64_t *stats3, int32_t *trace_buf,
+                int64_t trace_cap, int64_t *trace_len);
+
+static int solve_cnf(const batch_t *b, int nv, int64_t nc, const int64_t *cb,
+                     const int32_t *lits, uint8_t *model, int64_t *st) {
+  if (b->algo == 1) return oracle_cdcl(nv, nc, cb, lits, b->budget, model, st, NULL, 0, NULL);
+  return oracle_dpll(nv, nc, cb, lits, b->budget, model, st, NULL, 0, NULL);
+}
 
 static void solve_one(batch_t *b, int i) {
   int64_t st[3] = {0, 0, 0};
@@ -677,7 +688,7 @@ static void solve_one(batch_t *b, int i) {
     ocnf_t *c = oracle_encode(a, len);
     if (!c) { b->verdict[i] = V_ERROR; return; }
     uint8_t *model = (uint8_t *)malloc((size_t)c->nvars + 1);
-    int v = oracle_dpll(c->nvars, c->ncl, c->cb, c->lits, b->budget, model, st, NULL, 0, NULL);
+    int v = solve_cnf(b, c->nvars, c->ncl, c->cb, c->lits, model, st);
     b->verdict[i] = (uint8_t)v;
     if (b->cnf_size) { b->cnf_size[2 * i] = c->nvars; b->cnf_size[2 * i + 1] = c->ncl; }
     if (v == V_SAT && b->words) {
@@ -700,7 +711,7 @@ static void solve_one(batch_t *b, int i) {
     const int64_t *cb = b->cnf_cb + b->cnf_cb_off[i];
     int64_t nc = b->cnf_cb_off[i + 1] - b->cnf_cb_off[i] - 1;
     const int32_t *lits = b->cnf_lits + b->cnf_lit_off[i];
-    b->verdict[i] = (uint8_t)oracle_dpll(nv, nc, cb, lits, b->budget, NULL, st, NULL, 0, NULL);
+    b->verdict[i] = (uint8_t)solve_cnf(b, nv, nc, cb, lits, NULL, st);
   }
   if (b->stats) { b->stats[3 * i] = st[0]; b->stats[3 * i + 1] = st[1]; b->stats[3 * i + 2] = st[2]; }
 }
@@ -729,12 +740,13 @@ static void run_pool(batch_t *b, int nthreads) {
 }
 
 /* Encode + solve n queries. words: n x words_stride input words of each SAT
-   model (may be NULL). cnf_size: n x 2 (may be NULL). */
+   model (may be NULL). cnf_size: n x 2 (may be NULL). algo: 0 DPLL, 1 CDCL. */
 void oracle_solve_queries(int n, const int64_t *irs, const int64_t *ir_off, int nthreads,
                           int64_t budget, uint8_t *verdict, int64_t *stats,
-                          uint64_t *words, int words_stride, int64_t *cnf_size) {
+                          uint64_t *words, int words_stride, int64_t *cnf_size, int algo) {
   batch_t b;
   memset(&b, 0, sizeof(b));
+  b.algo = algo;
   b.irs = irs; b.ir_off = ir_off; b.n = n; b.budget = budget; b.verdict = verdict;
   b.stats = stats; b.words = words; b.words_stride = words_stride; b.cnf_size = cnf_size;
   run_pool(&b, nthreads);
@@ -744,9 +756,10 @@ void oracle_solve_queries(int n, const int64_t *irs, const int64_t *ir_off, int 
    relative to its own lits); lit_off[n] indexes lits. */
 void oracle_solve_cnfs(int n, const int32_t *nv, const int64_t *cb_off, const int64_t *cb,
                        const int64_t *lit_off, const int32_t *lits, int nthreads,
-                       int64_t budget, uint8_t *verdict, int64_t *stats) {
+                       int64_t budget, uint8_t *verdict, int64_t *stats, int algo) {
   batch_t b;
   memset(&b, 0, sizeof(b));
+  b.algo = algo;
   b.cnf_nv = nv; b.cnf_cb_off = cb_off; b.cnf_cb = cb; b.cnf_lit_off = lit_off;
   b.cnf_lits = lits; b.n = n; b.budget = budget; b.verdict = verdict; b.stats = stats;
   run_pool(&b, nthreads);

@@ -18,6 +18,7 @@ from workloads.ir import IR
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
+CDCL_SRC = os.path.join(ROOT, "oracle", "cdcl.c")
 
 MUTANTS = {
     "adder_drops_carry": (
@@ -48,12 +49,12 @@ def _build(src_text: str, tag: str) -> ctypes.CDLL:
         f.write(src_text)
     so = os.path.join(d, "lib.so")
     subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-fPIC", "-shared", "-pthread", "-w",
-                           "-o", so, c, "-lm"])
+                           "-o", so, c, CDCL_SRC, "-lm"])
     L = ctypes.CDLL(so)
     P = ctypes.c_void_p
     L.oracle_solve_queries.restype = None
     L.oracle_solve_queries.argtypes = [ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int64, P, P,
-                                       P, ctypes.c_int, P]
+                                       P, ctypes.c_int, P, ctypes.c_int]
     L.oracle_brute_force.restype = ctypes.c_int
     L.oracle_brute_force.argtypes = [P, ctypes.c_int64, ctypes.c_int, P]
     return L
@@ -67,7 +68,7 @@ def _solve(L, irs):
     buf = np.ascontiguousarray(np.concatenate(irs), np.int64)
     v = np.zeros(n, np.uint8)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    L.oracle_solve_queries(n, p(buf), p(offs), 4, 200000, p(v), None, None, 0, None)
+    L.oracle_solve_queries(n, p(buf), p(offs), 4, 200000, p(v), None, None, 0, None, 0)
     return v
 
 
