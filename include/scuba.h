@@ -52,12 +52,23 @@ enum {
   SCUBA_ERR_TOO_LARGE = -7  /* an instance exceeds the solver's size limits: max_vars
                                < 2^29, fewer than 2^32 literals per instance, and the
                                2-bit assignment of max_vars variables must fit a
-                               warp's share of shared memory (about 900k variables) */
+                               warp's share of shared memory (about 900k variables) */,
+  SCUBA_ERR_INTERNAL = -8   /* a device-side consistency check of the search failed
+                               (a library bug); the instance is left UNKNOWN */
 };
 
 /* Branching heuristics (Sec. VIII-style extensions are not in the paper; the
    paper's solver is a CPU CP-SAT call, Sec. V-B step 10). */
 enum { SCUBA_HEUR_ACTIVITY = 0, SCUBA_HEUR_LEARNED = 1 };
+
+/* Search algorithms (scuba_options.search). DPLL is the complete search of
+ * the paper's pipeline written out plainly (Sec. V-B, step 10); CDCL adds
+ * conflict-driven clause learning -- the paper's solver learns clauses
+ * internally without describing how; this is the standard first-UIP scheme:
+ * learned clauses with two watched literals in a per-warp arena,
+ * non-chronological backjumps, phase saving and Luby restarts. Verdicts are
+ * the same; only the work to reach them differs. */
+enum { SCUBA_SEARCH_DPLL = 0, SCUBA_SEARCH_CDCL = 1 };
 
 /*
  * A batch of CNF instances in CSR form. Array pointers are DEVICE pointers
@@ -129,10 +140,16 @@ typedef struct scuba_options {
   int32_t trail_placement;   /* 0: auto (global), 1: shared memory, 2: global memory */
   int64_t* finish_ns;        /* profiling, device [num_instances] or NULL: time from
                                 the start of the search to each verdict, in ns */
-  int64_t* profile;          /* profiling, device [8] or NULL, added to: subtrees
-                                shared, subtrees run, prefix literals shared, open
-                                depth left at each share, shares refused (ring
-                                full), idle polls */
+  int64_t* profile;          /* profiling, device [16] or NULL, added to: [0..5]
+                                subtrees shared, subtrees run, prefix literals
+                                shared, open depth left at each share, shares
+                                refused (ring full), idle polls; CDCL only, clock
+                                cycles of each warp's lane 0 in [8] propagation
+                                (all of it), [9] learned-clause watches (part of
+                                [8]), [10] conflict analysis, backjump and clause
+                                store, [11] decisions, [12] database maintenance;
+                                counts in [13] maintenance runs, [14] learned
+                                clauses stored */
   int64_t* stats;            /* device [num_instances*SCUBA_NSTATS], added to; may
                                 be NULL. Per instance: decisions, conflicts,
                                 propagations (trail literals processed),
@@ -148,6 +165,18 @@ typedef struct scuba_options {
                                      bits of each query (the encoder numbers them
                                      first); a feature of the branching network */
   const scuba_trace* trace;  /* host struct of device buffers, or NULL */
+  int32_t search;            /* SCUBA_SEARCH_DPLL (default) or SCUBA_SEARCH_CDCL. CDCL
+                                takes activity branching only (no trace, no network),
+                                shares hard instances as cubes (split, split_min and
+                                split_interval as for DPLL), and counts
+                                decision_budget in CONFLICTS per instance */
+  int32_t restart_unit;      /* CDCL: conflicts per unit of the Luby restart sequence;
+                                0: default 100 */
+  int64_t learnt_words;      /* CDCL: learned-clause arena of each worker warp, in
+                                32-bit words (a clause of n literals takes 4 + n
+                                rounded up to 4), and as many 8-byte watch entries;
+                                0: default 2^18. At least max(max_vars + 8, 64),
+                                below 2^30 */
 } scuba_options;
 
 /* Number of int64 counters per instance in scuba_options.stats. */

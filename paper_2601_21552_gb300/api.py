@@ -116,6 +116,9 @@ class Trace:
         return min(c[0], self.max_nodes), min(c[1], self.max_rows)
 
 
+SEARCH = {"dpll": B.SCUBA_SEARCH_DPLL, "cdcl": B.SCUBA_SEARCH_CDCL}
+
+
 def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
             time_budget_ms: int = 0, split: bool = True, warps_per_block: int = 0,
             blocks_per_sm: int = 0, split_interval: int = 0, split_min: int = 0, trail_placement: int = 0, stats: torch.Tensor | None = None,
@@ -123,9 +126,13 @@ def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
             learned_depth: int = 0, abort_flag_ptr: int | None = None,
             events: tuple | None = None, finish_ns: torch.Tensor | None = None,
             profile: torch.Tensor | None = None, num_inputs: torch.Tensor | None = None,
-            trace: "Trace | None" = None) -> B.scuba_options:
+            trace: "Trace | None" = None, search: str | int = "dpll",
+            restart_unit: int = 0, learnt_words: int = 0) -> B.scuba_options:
     o = B.scuba_options_init()
     o.heuristic = heuristic
+    o.search = SEARCH[search] if isinstance(search, str) else int(search)
+    o.restart_unit = restart_unit
+    o.learnt_words = learnt_words
     o.decision_budget = decision_budget
     o.time_budget_ms = time_budget_ms
     o.split = 1 if split else 0

@@ -26,7 +26,9 @@ SCUBA_UNSAT, SCUBA_SAT, SCUBA_UNKNOWN = 0, 1, 2
 SCUBA_OK = 0
 SCUBA_ERR_ARG, SCUBA_ERR_CUDA, SCUBA_ERR_NOMEM = -1, -2, -3
 SCUBA_ERR_TIMEOUT, SCUBA_ERR_MALFORMED, SCUBA_ERR_ABORTED, SCUBA_ERR_TOO_LARGE = -4, -5, -6, -7
+SCUBA_ERR_INTERNAL = -8
 SCUBA_HEUR_ACTIVITY, SCUBA_HEUR_LEARNED = 0, 1
+SCUBA_SEARCH_DPLL, SCUBA_SEARCH_CDCL = 0, 1
 
 _vp = ctypes.c_void_p
 _i32, _i64 = ctypes.c_int32, ctypes.c_int64
@@ -47,7 +49,8 @@ class scuba_options(ctypes.Structure):
                 ("profile", _vp),
                 ("stats", _vp), ("order", _vp), ("abort_flag", _vp),
                 ("search_event_begin", _vp), ("search_event_end", _vp),
-                ("inst_num_inputs", _vp), ("trace", _vp)]
+                ("inst_num_inputs", _vp), ("trace", _vp), ("search", _i32),
+                ("restart_unit", _i32), ("learnt_words", _i64)]
 
 
 class scuba_trace(ctypes.Structure):

@@ -44,8 +44,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     defs = []
-    if os.environ.get("SCUBA_LEARNED_MINBLOCKS"):
-        defs.append("-DSCUBA_LEARNED_MINBLOCKS=" + str(int(os.environ["SCUBA_LEARNED_MINBLOCKS"])))
+    for var in ("SCUBA_LEARNED_MINBLOCKS", "SCUBA_CDCL_MINBLOCKS"):
+        if os.environ.get(var):
+            defs.append(f"-D{var}=" + str(int(os.environ[var])))
     jobs = []
     objs = []
     for s in HOST_SRCS:

@@ -1,0 +1,875 @@
+// cdcl.cuh -- conflict-driven clause learning mode of the persistent search
+// (included by solver.cu after the DPLL search; same prep layout, shared
+// assignment, BCP frontier rounds and worker loop).
+//
+// The paper's solver (Sec. V-B, OR-Tools' SAT solver) learns clauses
+// internally and says no more about it; this mode puts the textbook
+// first-UIP scheme on top of the GPU propagation of the DPLL mode:
+//
+//  * Every assigned variable keeps its reason (the occurrence entry or clause
+//    reference that implied it), its decision level and the BCP round it was
+//    assigned in (stamp).
+//  * Propagation rounds are frontier-parallel, so two lanes can assign
+//    variables of the same round in either trail order. An implication may
+//    therefore only rely on false literals assigned BEFORE the current round;
+//    a clause whose unit-ness depends on a literal falsified during the round
+//    is left for the next round, where that literal's own occurrence list
+//    brings it back. Every reason then precedes its literal on the trail, and
+//    the trail is a topological order of the implication graph. Conflicts
+//    need no such rule: a falsified clause is a conflict whenever found.
+//  * Learned clauses live in a per-warp arena with two watched literals per
+//    clause. Each literal's watch list is an array in a per-warp pool (grown
+//    by doubling); an entry is {clause, blocker}, the blocker being a literal
+//    of the clause (the other watch when the entry was made) whose truth
+//    settles the clause without reading it. After the static occurrence
+//    entries of each frontier batch, the watchers of every literal in the
+//    batch are spread over the 32 lanes like the static entries. A clause
+//    can sit on two lists of one batch only when both its watches are false;
+//    a lane then takes a per-clause lock first, and the loser retries after
+//    the winner has moved its watch. Moved watches are appended to their new
+//    lists one at a time (the warp copies a list when it grows) and the
+//    batch's own lists are compacted afterwards.
+//  * Conflict analysis resolves the falsified clause with the reasons of
+//    current-level literals, newest first on the trail, until one
+//    current-level literal (the first UIP) is left; the lanes take the
+//    literals of each clause and a warp-wide backward scan of the trail
+//    finds the next literal to resolve. Every variable met is bumped.
+//  * Hard instances are shared cube-and-conquer style through the DPLL mode's
+//    job ring: a busy warp that sees idle warps gives away the negation of
+//    its first free decision, together with the assumptions above it, as a
+//    cube, and keeps that decision as one more assumption itself (backjumps
+//    and restarts never undo assumptions). An instance is UNSAT once every
+//    cube is; a cube starts from its donor's activities with no learned
+//    clauses.
+//  * The search backjumps to the second-highest level of the learned clause
+//    and asserts its UIP literal there; decisions take the saved phase (the
+//    variable's last value, false at first); restarts follow the Luby
+//    sequence times `restart_unit` conflicts. The first restart after 2000
+//    conflicts (then 2300, 2600, ... more) also halves the learned clauses,
+//    keeping the newer half and every clause of LBD <= 3 (the number of
+//    distinct decision levels in it at learning time, after Glucose). When
+//    the arena or the watch pool runs out the same reduction happens at once;
+//    if even that does not fit, every learned clause is dropped (all of them
+//    are implied by the formula, so any of this is sound).
+//
+// Clause arena layout (32-bit words, 16-byte aligned clauses): [len, lock, 0,
+// 0, lit0 .. lit_{len-1}, padding to a multiple of 4]; lit0 and lit1 are the
+// watched literals.
+
+constexpr uint32_t LEARNT_REF = 0xC0000000u;  // clause reference: learned clause at offset
+constexpr uint32_t CD_HDR = 4;
+constexpr uint64_t WATCH_GONE = ~0ull;     // tombstone of a moved watch entry
+constexpr uint32_t STAMP_OPEN = 0xffffffffu;  // stamp of an unassigned variable
+constexpr uint8_t MK_PHASE = 1, MK_SEEN = 2;
+
+// Profile counters (only when the caller passed a profile array): lane 0
+// adds the clock cycles of each phase to its warp's WarpShared::cyc.
+enum { PF_BCP = 0, PF_LEARNED = 1, PF_ANALYZE = 2, PF_DECIDE = 3, PF_DB = 4, PF_NDB = 5,
+       PF_NLEARNT = 6 };
+
+__device__ __forceinline__ long long pf_now(const Solve& S) {
+  return S.prof ? clock64() : 0;
+}
+
+__device__ __forceinline__ void pf_add(const Solve& S, Warp& w, int k, long long t0) {
+  if (S.prof && w.lane == 0) w.ws->cyc[k] += (unsigned long long)(clock64() - t0);
+}
+
+__device__ __forceinline__ bool is_learnt_ref(uint32_t a) {
+  return a != NONE && (a & LEARNT_REF) == LEARNT_REF;
+}
+
+struct WList {       // one literal's learned watch list in the pool
+  uint32_t off, len, cap, pad;
+};
+
+struct CdWarp {
+  uint64_t* reason;   // [V] occurrence entry {a, b} or clause reference (low word)
+  uint32_t* level;    // [V]
+  uint32_t* stamp;    // [V] BCP round of the assignment, STAMP_OPEN when unassigned
+  uint8_t* mark;      // [V] MK_PHASE saved phase, MK_SEEN during analysis
+  WList* wl;          // [2V] learned watch list per literal code
+  uint64_t* pool;     // [pool_cap] watch entries {clause, blocker}
+  uint32_t* arena;    // [arena_words]
+  uint32_t* cl_off;   // [arena_words / 8] arena offset of each learned clause, oldest first
+  uint32_t* learnt;   // [V] clause under construction
+  uint32_t arena_words, pool_cap;
+  uint32_t top;       // first free arena word
+  uint32_t ncl;       // learned clauses in the arena
+  uint32_t pool_top;  // first free pool entry
+  uint32_t round;     // current BCP round
+  uint32_t full;      // the pool ran out during propagation: drop the learned clauses
+};
+
+// Assign l with reason `why` at the current level. False on a clash.
+__device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64_t why) {
+  const uint32_t v = l >> 1;
+  const uint32_t sh = (v & 15u) * 2u;
+  const uint32_t mask = ((l & 1u) ? 2u : 1u) << sh;
+  const uint32_t old = atomicOr(&w.asg[v >> 4], mask);
+  const uint32_t ob = (old >> sh) & 3u;
+  if (ob == 0u) {
+    const uint32_t pos = atomicAdd(&w.ws->tail, 1u);
+    w.trail[pos] = l;
+    cd.reason[v] = why;
+    cd.level[v] = w.nd;
+    cd.stamp[v] = cd.round;
+    return true;
+  }
+  if (ob == (mask >> sh)) return true;
+  if ((old & mask) == 0u) atomicAnd(&w.asg[v >> 4], ~mask);
+  return false;
+}
+
+// Was (assigned) literal l set during the current round? An unassigned
+// variable's stamp is STAMP_OPEN, and a variable claimed this round holds
+// STAMP_OPEN or the current round until its claimer's store lands: both read
+// as fresh.
+__device__ __forceinline__ bool fresh(const CdWarp& cd, uint32_t l) {
+  return *(volatile const uint32_t*)&cd.stamp[l >> 1] >= cd.round;
+}
+
+__device__ void eval_long_cd(Warp& w, CdWarp& cd, uint32_t local) {
+  const int64_t c = w.c0 + local;
+  const int64_t b = w.cb[c], e = w.cb[c + 1];
+  uint32_t open_lit = NONE;
+  int n_open = 0;
+  for (int64_t q = b; q < e; q++) {
+    const uint32_t x = code_of(__ldg(&w.lits[q]));
+    const uint32_t vx = lit_value(w.asg, x);
+    if (vx == LV_T || vx == LV_X) return;
+    if (vx == LV_U && x != open_lit) {
+      n_open++;
+      open_lit = x;
+      if (n_open > 1) return;
+    }
+  }
+  if (n_open == 0) {
+    record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
+    return;
+  }
+  for (int64_t q = b; q < e; q++) {
+    const uint32_t x = code_of(__ldg(&w.lits[q]));
+    if (x != open_lit && fresh(cd, x)) return;  // next round
+  }
+  if (!imply_cd(w, cd, open_lit, (uint64_t)(LONG_CLAUSE | local)))
+    record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
+}
+
+// One occurrence entry of the falsified (old) literal f.
+__device__ __forceinline__ void eval_entry_cd(Warp& w, CdWarp& cd, uint32_t f, uint64_t e) {
+  const uint32_t a = (uint32_t)e, b = (uint32_t)(e >> 32);
+  if (a & LONG_CLAUSE) {
+    eval_long_cd(w, cd, a & ~LONG_CLAUSE);
+    return;
+  }
+  const uint32_t va = lit_value(w.asg, a);
+  if (b == NONE) {  // binary (f | a): a's reason is {f}
+    if (va == LV_T || va == LV_X) return;
+    if (va == LV_F || !imply_cd(w, cd, a, (uint64_t)f | ((uint64_t)NONE << 32)))
+      record_conflict(w, f, a, NONE);
+    return;
+  }
+  const uint32_t vb = lit_value(w.asg, b);  // ternary (f | a | b)
+  if (va == LV_T || vb == LV_T || va == LV_X || vb == LV_X) return;
+  if (va == LV_F && vb == LV_F) {
+    record_conflict(w, f, a, b);
+  } else if (va == LV_F) {
+    if (fresh(cd, a)) return;
+    if (!imply_cd(w, cd, b, (uint64_t)f | ((uint64_t)a << 32))) record_conflict(w, f, a, b);
+  } else if (vb == LV_F) {
+    if (fresh(cd, b)) return;
+    if (!imply_cd(w, cd, a, (uint64_t)f | ((uint64_t)b << 32))) record_conflict(w, f, a, b);
+  }
+}
+
+// Append entry e to literal g's watch list (all lanes, uniform arguments).
+__device__ void wl_append(Warp& w, CdWarp& cd, uint32_t g, uint64_t e) {
+  if (cd.full) return;
+  WList L = cd.wl[g];  // last written before a __syncwarp
+  if (L.len == L.cap) {
+    const uint32_t ncap = L.cap ? 2u * L.cap : 8u;
+    if ((uint64_t)cd.pool_top + ncap > cd.pool_cap) {
+      cd.full = 1;
+      if (w.lane == 0) record_conflict(w, NONE, NONE, NONE);  // ends this BCP
+      __syncwarp();
+      return;
+    }
+    const uint32_t noff = cd.pool_top;
+    cd.pool_top += ncap;
+    for (uint32_t k = w.lane; k < L.len; k += 32) cd.pool[noff + k] = cd.pool[L.off + k];
+    L.off = noff;
+    L.cap = ncap;
+  }
+  __syncwarp();
+  if (w.lane == 0) {
+    cd.pool[L.off + L.len] = e;
+    L.len++;
+    cd.wl[g] = L;
+  }
+  __syncwarp();
+}
+
+// First position >= 2 of a learned clause whose literal passes ok(), NONE if
+// none does. Literals are read 8 at a time (two 16-byte loads; clauses are
+// 16-byte aligned and padded), and the 8 tests are made before the first
+// hit is picked, so that their loads are in flight together.
+template <class Ok>
+__device__ __forceinline__ uint32_t scan_clause(const uint32_t* lits, uint32_t len, Ok&& ok) {
+  const uint4* L4 = reinterpret_cast<const uint4*>(lits);
+  for (uint32_t q = 0; q < len; q += 8) {
+    const uint4 a = L4[q >> 2];
+    const uint4 b = q + 4 < len ? L4[(q >> 2) + 1] : make_uint4(NONE, NONE, NONE, NONE);
+    const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t hit = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      if (q + i >= 2 && q + i < len && ok(x[i])) hit |= 1u << i;
+    if (hit) return q + __ffs(hit) - 1;
+  }
+  return NONE;
+}
+
+// One watch entry (clause c, blocker) of the falsified literal f, at pool
+// index at. Returns the literal the watch moved to (NONE if it stayed) and
+// the entry for that literal's list.
+__device__ uint32_t visit_learnt(Warp& w, CdWarp& cd, uint32_t f, uint32_t at, uint32_t c,
+                                 uint64_t& moved_entry) {
+  uint32_t* C = cd.arena + c;
+  const uint32_t l0 = C[CD_HDR], l1 = C[CD_HDR + 1];
+  const uint32_t which = l0 == f ? 0u : 1u;
+  const uint32_t other = which ? l0 : l1;
+  const uint32_t vo = lit_value(w.asg, other);
+  if (vo == LV_T) {
+    cd.pool[at] = (uint64_t)c | ((uint64_t)other << 32);  // new blocker
+    return NONE;
+  }
+  // a new watch among lit2..: first a literal that is not false, else one
+  // falsified during this round (its own list brings the clause back)
+  const uint32_t len = C[0];
+  const uint32_t* lits = C + CD_HDR;
+  uint32_t k = scan_clause(lits, len, [&](uint32_t x) { return lit_value(w.asg, x) != LV_F; });
+  if (k == NONE) k = scan_clause(lits, len, [&](uint32_t x) { return fresh(cd, x); });
+  if (k != NONE) {
+    const uint32_t g = C[CD_HDR + k];
+    C[CD_HDR + k] = f;
+    C[CD_HDR + which] = g;
+    cd.pool[at] = WATCH_GONE;
+    moved_entry = (uint64_t)c | ((uint64_t)other << 32);
+    return g;
+  }
+  if (vo == LV_F) {
+    record_conflict(w, LEARNT_REF | c, NONE, NONE);
+  } else if (vo == LV_U) {
+    if (!imply_cd(w, cd, other, (uint64_t)(LEARNT_REF | c)))
+      record_conflict(w, LEARNT_REF | c, NONE, NONE);
+  }  // LV_X: the clash is recorded by the lane that claimed `other`
+  return NONE;
+}
+
+// Learned clauses watching the literals falsified by trail[base .. base+nlit).
+__device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t base, uint32_t nlit) {
+  __syncwarp();
+  if (cd.top == 0) return;  // no learned clauses
+  const long long t0 = pf_now(*w.S);
+  uint32_t f = 0, beg = 0, cnt = 0;
+  if (w.lane < nlit) {
+    f = w.trail[base + w.lane] ^ 1u;
+    const WList L = cd.wl[f];
+    beg = L.off;
+    cnt = L.len;
+  }
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, inc, d);
+    if (w.lane >= d) inc += y;
+  }
+  const uint32_t excl = inc - cnt;
+  const uint32_t total = __shfl_sync(FULL, inc, 31);
+  WCOUNT(w, visits, total);
+  uint32_t dirty = 0;  // lists that lost an entry
+  for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+    const uint32_t e = e0 + w.lane;
+    int lo_j = 0, hi_j = 31;  // owner: smallest lane j with inc_j > e
+#pragma unroll
+    for (int s2 = 0; s2 < 5; s2++) {
+      const int mid = (lo_j + hi_j) >> 1;
+      const uint32_t v = __shfl_sync(FULL, inc, mid);
+      if (v > e) hi_j = mid; else lo_j = mid + 1;
+      if (lo_j > hi_j) lo_j = hi_j;
+    }
+    const uint32_t jbeg = __shfl_sync(FULL, beg, lo_j);
+    const uint32_t jex = __shfl_sync(FULL, excl, lo_j);
+    const uint32_t jf = __shfl_sync(FULL, f, lo_j);
+    bool pending = false;
+    uint32_t at = 0, c = 0;
+    if (e < total) {
+      at = jbeg + (e - jex);
+      const uint64_t ent = cd.pool[at];
+      c = (uint32_t)ent;
+      pending = lit_value(w.asg, (uint32_t)(ent >> 32)) != LV_T;  // blocker
+    }
+    uint32_t g = NONE;
+    uint64_t moved = 0;
+    // both watches false: the clause may be on two lists of this batch, so
+    // the lane locks it; a loser retries after the winner's pass
+    while (__any_sync(FULL, pending)) {
+      if (pending) {
+        volatile uint32_t* C = cd.arena + c;
+        const uint32_t other = C[CD_HDR] == jf ? C[CD_HDR + 1] : C[CD_HDR];
+        bool go = true, locked = false;
+        if (lit_value(w.asg, other) == LV_F) {
+          locked = atomicCAS((uint32_t*)&C[1], 0u, 1u) == 0u;
+          go = locked;
+        }
+        if (go) {
+          g = visit_learnt(w, cd, jf, at, c, moved);
+          if (locked) {
+            __threadfence_block();
+            atomicExch((uint32_t*)&C[1], 0u);
+          }
+          pending = false;
+        }
+      }
+      __syncwarp();
+    }
+    dirty |= __reduce_or_sync(FULL, g != NONE ? (1u << lo_j) : 0u);
+    uint32_t movers = __ballot_sync(FULL, g != NONE);
+    while (movers) {
+      const int j = __ffs(movers) - 1;
+      movers &= movers - 1u;
+      const uint32_t gj = __shfl_sync(FULL, g, j);
+      const uint64_t mj = __shfl_sync(FULL, moved, j);
+      wl_append(w, cd, gj, mj);
+    }
+  }
+  // compact the lists that lost entries (lane j owns frontier literal j)
+  if (w.lane < nlit && ((dirty >> w.lane) & 1u) && !cd.full) {
+    uint32_t keep = 0;
+    for (uint32_t k = 0; k < cnt; k++) {
+      const uint64_t ent = cd.pool[beg + k];
+      if (ent != WATCH_GONE) cd.pool[beg + keep++] = ent;
+    }
+    cd.wl[f].len = keep;
+  }
+  __syncwarp();
+  pf_add(*w.S, w, PF_LEARNED, t0);
+}
+
+__device__ bool bcp_cd(Warp& w, CdWarp& cd) {
+  return bcp_rounds(
+      w, [&](uint32_t f, uint64_t e) { eval_entry_cd(w, cd, f, e); }, [&] { cd.round++; },
+      [&](uint32_t base, uint32_t nlit) { learned_batch(w, cd, base, nlit); });
+}
+
+// First-UIP analysis of the recorded conflict (all lanes). Leaves the learned
+// clause in cd.learnt[0 .. n): the asserting literal first, then a literal of
+// the backjump level; returns n, the backjump level in blev and the clause's
+// LBD (distinct decision levels, counted per group of 32 literals) in lbd.
+// Returns 0 if a consistency check fails (seen marks may then be left set).
+__device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lbd) {
+  const uint32_t lvl = w.nd;
+  uint32_t n = 1, path = 0, p = NONE;
+  uint32_t r0 = w.ws->cl[0], r1 = w.ws->cl[1], r2 = w.ws->cl[2];
+  int64_t idx = (int64_t)*(volatile uint32_t*)&w.ws->tail - 1;
+  bool big = false;
+  for (;;) {
+    // the literals of the clause: static entry (up to three codes), a long
+    // clause of the caller's CSR, or a learned clause
+    const uint32_t* src = nullptr;
+    const int32_t* csr = nullptr;
+    uint32_t cnt = 3;
+    if (is_learnt_ref(r0)) {
+      const uint32_t off = r0 & ~LEARNT_REF;
+      cnt = cd.arena[off];
+      src = cd.arena + off + CD_HDR;
+    } else if (r0 & LONG_CLAUSE) {
+      const int64_t cl = w.c0 + (r0 & ~LONG_CLAUSE);
+      const int64_t b = w.cb[cl];
+      csr = w.lits + b;
+      cnt = (uint32_t)(w.cb[cl + 1] - b);
+    }
+    for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
+      const uint32_t k = k0 + w.lane;
+      uint32_t q = NONE;
+      if (k < cnt) q = src ? src[k] : csr ? code_of(csr[k]) : (k == 0 ? r0 : k == 1 ? r1 : r2);
+      const uint32_t v = q >> 1;
+      bool take = q != NONE && (p == NONE || v != (p >> 1));
+      if (take) take = !(cd.mark[v] & MK_SEEN);
+      uint32_t lv = 0;
+      if (take) {
+        lv = cd.level[v];
+        take = lv > 0;
+      }
+      // one lane per variable (a long clause may repeat a literal)
+      const uint32_t grp = __match_any_sync(FULL, take ? v : NONE);
+      if (take && __ffs(grp) - 1 != w.lane) take = false;
+      if (take) {
+        cd.mark[v] |= MK_SEEN;
+        const float a = w.act[v] + w.inc;
+        w.act[v] = a;
+        big |= a > 1e20f;
+      }
+      path += __popc(__ballot_sync(FULL, take && lv >= lvl));
+      const uint32_t lowm = __ballot_sync(FULL, take && lv < lvl);
+      if (take && lv < lvl) cd.learnt[n + __popc(lowm & ((1u << w.lane) - 1u))] = q;
+      n += __popc(lowm);
+      __syncwarp();
+    }
+    // the newest seen literal on the trail is the next to resolve; a
+    // conflict without a current-level literal, or a scan that runs off the
+    // trail, means the search state is inconsistent: give up (n = 0)
+    if (path == 0) return 0;
+    for (;;) {
+      if (idx < 0) return 0;
+      const int64_t pos = idx - w.lane;
+      bool s = false;
+      if (pos >= 0) s = (cd.mark[w.trail[pos] >> 1] & MK_SEEN) != 0;
+      const uint32_t m = __ballot_sync(FULL, s);
+      if (m) {
+        idx -= __ffs(m) - 1;
+        break;
+      }
+      idx -= 32;
+    }
+    p = w.trail[idx];
+    idx--;
+    __syncwarp();
+    if (w.lane == 0) cd.mark[p >> 1] &= (uint8_t)~MK_SEEN;
+    __syncwarp();
+    if (--path == 0) break;
+    const uint64_t why = cd.reason[p >> 1];
+    r0 = (uint32_t)why;
+    r1 = (uint32_t)(why >> 32);
+    r2 = NONE;
+  }
+  if (w.lane == 0) cd.learnt[0] = p ^ 1u;
+  // backjump level: the highest level among learnt[1..n), moved to position 1
+  uint32_t best_l = 0, best_k = 1, levels = 1;  // learnt[0] is alone at level lvl
+  for (uint32_t k0 = 1; k0 < n; k0 += 32) {
+    const uint32_t k = k0 + w.lane;
+    uint32_t lv = NONE;
+    if (k < n) {
+      const uint32_t q = cd.learnt[k];
+      lv = cd.level[q >> 1];
+      if (lv > best_l) {
+        best_l = lv;
+        best_k = k;
+      }
+      cd.mark[q >> 1] &= (uint8_t)~MK_SEEN;
+    }
+    const uint32_t grp = __match_any_sync(FULL, lv);
+    levels += __popc(__ballot_sync(FULL, k < n && __ffs(grp) - 1 == w.lane));
+  }
+  lbd = levels;
+  for (int d = 16; d > 0; d >>= 1) {
+    const uint32_t ol = __shfl_xor_sync(FULL, best_l, d);
+    const uint32_t ok = __shfl_xor_sync(FULL, best_k, d);
+    if (ol > best_l || (ol == best_l && ok < best_k)) {
+      best_l = ol;
+      best_k = ok;
+    }
+  }
+  __syncwarp();
+  if (w.lane == 0 && n > 2 && best_k != 1) {
+    const uint32_t t = cd.learnt[1];
+    cd.learnt[1] = cd.learnt[best_k];
+    cd.learnt[best_k] = t;
+  }
+  big = __any_sync(FULL, big);
+  if (big) {
+    for (uint32_t v = w.lane; v < w.V; v += 32) w.act[v] *= 1e-20f;
+    w.inc *= 1e-20f;
+  }
+  __syncwarp();
+  blev = best_l;
+  return n;
+}
+
+// Undo every assignment above level lev, saving phases.
+__device__ void backjump_cd(Warp& w, CdWarp& cd, uint32_t lev) {
+  if (w.nd <= lev) return;
+  const uint32_t pos = w.dstack[lev];
+  const uint32_t tail = *(volatile uint32_t*)&w.ws->tail;
+  WCOUNT(w, undone, tail - pos);
+  for (uint32_t t = pos + w.lane; t < tail; t += 32) {
+    const uint32_t l = w.trail[t], v = l >> 1;
+    atomicAnd(&w.asg[v >> 4], ~(3u << ((v & 15u) * 2u)));
+    cd.stamp[v] = STAMP_OPEN;
+    cd.mark[v] = (l & 1u) ? 0 : MK_PHASE;
+  }
+  __syncwarp();
+  if (w.lane == 0) w.ws->tail = pos;
+  __syncwarp();
+  w.nd = lev;
+  w.head = pos;
+}
+
+// Arena words a learned clause of n literals takes.
+__device__ __forceinline__ uint32_t clause_words(uint32_t n) {
+  return CD_HDR + ((n + 3u) & ~3u);
+}
+
+// Store learnt[0..n) (n >= 2) at the arena top and watch its first two
+// literals. The caller checked the arena has room; the pool may run out
+// (cd.full).
+__device__ uint32_t add_learnt(Warp& w, CdWarp& cd, uint32_t n, uint32_t lbd) {
+  const uint32_t c = cd.top;
+  for (uint32_t k = w.lane; k < ((n + 3u) & ~3u); k += 32)
+    cd.arena[c + CD_HDR + k] = k < n ? cd.learnt[k] : NONE;
+  if (w.lane == 0) {
+    cd.arena[c] = n;
+    cd.arena[c + 1] = 0u;
+    cd.arena[c + 2] = lbd;
+    cd.arena[c + 3] = 0u;
+  }
+  if (w.lane == 0) {
+    cd.cl_off[cd.ncl] = c;
+    if (w.S->prof) w.ws->cyc[PF_NLEARNT]++;
+  }
+  __syncwarp();
+  cd.top = c + clause_words(n);
+  cd.ncl++;
+  const uint32_t l0 = cd.learnt[0], l1 = cd.learnt[1];
+  wl_append(w, cd, l0, (uint64_t)c | ((uint64_t)l1 << 32));
+  wl_append(w, cd, l1, (uint64_t)c | ((uint64_t)l0 << 32));
+  return c;
+}
+
+__device__ void clear_learnts(Warp& w, CdWarp& cd) {
+  for (uint32_t k = w.lane; k < 2u * w.V; k += 32) cd.wl[k] = WList{0u, 0u, 0u, 0u};
+  cd.top = 0;
+  cd.ncl = 0;
+  cd.pool_top = 0;
+  cd.full = 0;
+  __syncwarp();
+}
+
+// Learned-clause database maintenance at the bottom level (no reason above it
+// refers to a learned clause). With drop_half, keep the newer half of the
+// clauses and every clause whose LBD is at most 3 (the "glue" clauses that
+// tie few decision levels together); otherwise keep them all.
+// Kept clauses move down the arena in order; then every watch list is built
+// afresh from the clauses' first two literals (count, scan, fill), which
+// also compacts the pool. Returns false when the lists would take more than
+// half of the pool.
+__device__ bool reduce_db(Warp& w, CdWarp& cd, bool drop_half) {
+  const uint32_t n = cd.ncl;
+  uint32_t run_words = 0, run_cl = 0;
+  for (uint32_t k0 = 0; k0 < n; k0 += 32) {
+    const uint32_t k = k0 + w.lane;
+    uint32_t off = 0, words = 0;
+    bool keep = false;
+    if (k < n) {
+      off = cd.cl_off[k];
+      const uint32_t len = cd.arena[off];
+      keep = !drop_half || k >= n / 2 || cd.arena[off + 2] <= 3u;
+      if (keep) words = clause_words(len);
+    }
+    uint32_t inc = words;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, d);
+      if (w.lane >= d) inc += y;
+    }
+    const uint32_t dst = run_words + inc - words;
+    const uint32_t km = __ballot_sync(FULL, keep);
+    __syncwarp();
+    // move the kept clauses down one at a time, in order (dst <= src)
+    for (uint32_t m = km; m; m &= m - 1u) {
+      const int j = __ffs(m) - 1;
+      const uint32_t src = __shfl_sync(FULL, off, j), to = __shfl_sync(FULL, dst, j);
+      const uint32_t wd = __shfl_sync(FULL, words, j);
+      if (src != to)
+        for (uint32_t q0 = 0; q0 < wd; q0 += 32) {
+          const uint32_t q = q0 + w.lane;
+          const uint32_t x = q < wd ? cd.arena[src + q] : 0u;
+          __syncwarp();
+          if (q < wd) cd.arena[to + q] = x;
+          __syncwarp();
+        }
+    }
+    if (keep) cd.cl_off[run_cl + __popc(km & ((1u << w.lane) - 1u))] = dst;
+    run_words += __shfl_sync(FULL, inc, 31);
+    run_cl += __popc(km);
+    __syncwarp();
+  }
+  cd.top = run_words;
+  cd.ncl = run_cl;
+  // watch lists: count, exclusive scan of capacities, fill
+  const uint32_t nl = 2u * w.V;
+  for (uint32_t k = w.lane; k < nl; k += 32) cd.wl[k] = WList{0u, 0u, 0u, 0u};
+  __syncwarp();
+  for (uint32_t k = w.lane; k < run_cl; k += 32) {
+    const uint32_t c = cd.cl_off[k];
+    atomicAdd(&cd.wl[cd.arena[c + CD_HDR]].len, 1u);
+    atomicAdd(&cd.wl[cd.arena[c + CD_HDR + 1]].len, 1u);
+  }
+  __syncwarp();
+  uint32_t base = 0;
+  for (uint32_t k0 = 0; k0 < nl; k0 += 32) {
+    const uint32_t k = k0 + w.lane;
+    const uint32_t len = k < nl ? cd.wl[k].len : 0u;
+    const uint32_t cap = len ? len + max(4u, len / 2u) : 0u;
+    uint32_t inc = cap;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, d);
+      if (w.lane >= d) inc += y;
+    }
+    if (k < nl) cd.wl[k] = WList{base + inc - cap, 0u, cap, 0u};
+    base += __shfl_sync(FULL, inc, 31);
+  }
+  __syncwarp();
+  cd.pool_top = 0;
+  cd.full = 0;
+  if (base > cd.pool_cap / 2) return false;  // leave room for the lists to grow
+  for (uint32_t k = w.lane; k < run_cl; k += 32) {
+    const uint32_t c = cd.cl_off[k];
+    const uint32_t l0 = cd.arena[c + CD_HDR], l1 = cd.arena[c + CD_HDR + 1];
+    const uint32_t p0 = atomicAdd(&cd.wl[l0].len, 1u);
+    cd.pool[cd.wl[l0].off + p0] = (uint64_t)c | ((uint64_t)l1 << 32);
+    const uint32_t p1 = atomicAdd(&cd.wl[l1].len, 1u);
+    cd.pool[cd.wl[l1].off + p1] = (uint64_t)c | ((uint64_t)l0 << 32);
+  }
+  cd.pool_top = base;
+  __syncwarp();
+  return true;
+}
+
+// Bring the database back within its limits at the bottom level: compact
+// (drop_half false) or halve it, and if the lists still do not fit, drop it.
+// Afterwards the bottom levels are propagated again from the first trail
+// entry, over the rebuilt watch lists too.
+__device__ void maintain_db(Warp& w, CdWarp& cd, bool drop_half) {
+  const long long t0 = pf_now(*w.S);
+  if (w.S->prof && w.lane == 0) w.ws->cyc[PF_NDB]++;
+  backjump_cd(w, cd, w.nd_fixed);
+  if (!reduce_db(w, cd, drop_half) && (drop_half || !reduce_db(w, cd, true)))
+    clear_learnts(w, cd);
+  if (w.lane == 0) w.ws->conflict = 0;
+  __syncwarp();
+  w.head = 0;
+  pf_add(*w.S, w, PF_DB, t0);
+}
+
+// luby(i), i >= 1: 1 1 2 1 1 2 4 1 1 2 1 1 2 4 8 ...: luby(2^k - 1) = 2^(k-1);
+// otherwise the sequence repeats itself, luby(i) = luby(i - 2^(k-1) + 1) for
+// 2^(k-1) <= i < 2^k - 1 (Luby, Sinclair and Zuckerman).
+__device__ uint32_t luby_cd(uint32_t i) {
+  for (;;) {
+    uint32_t k = 1;
+    while (k < 31 && (1u << k) - 1u < i) k++;
+    if (i == (1u << k) - 1u || k == 31) return 1u << (k - 1);
+    i -= (1u << (k - 1)) - 1u;
+  }
+}
+
+// One job: an instance, or a cube of it (the job's literals as assumptions,
+// from the subtree-sharing ring), start to verdict. Returns SAT, UNSAT (for a
+// cube: no model extends it) or UNKNOWN.
+__device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const TakenJob* job,
+                        int& abort_code) {
+  CdWarp cd;
+  cd.reason = S.cd_reason + slot * S.vmax;
+  cd.level = S.cd_level + slot * S.vmax;
+  cd.stamp = S.cd_stamp + slot * S.vmax;
+  cd.mark = S.cd_mark + slot * S.vmax;
+  cd.wl = S.cd_wl + slot * 2 * S.vmax;
+  cd.pool = S.cd_pool + slot * S.cd_pool_cap;
+  cd.arena = S.cd_arena + slot * S.cd_arena_words;
+  cd.learnt = S.cd_learnt + slot * S.vmax;
+  cd.cl_off = S.cd_clidx + slot * (S.cd_arena_words / 8);
+  cd.arena_words = (uint32_t)S.cd_arena_words;
+  cd.ncl = 0;
+  cd.pool_cap = (uint32_t)S.cd_pool_cap;
+  cd.top = 0;
+  cd.pool_top = 0;
+  cd.round = 1;
+  cd.full = 0;
+  w.inst = inst;
+  w.V = (uint32_t)S.nv[inst];
+  w.c0 = S.icb[inst];
+  w.occ = S.occ_begin + S.occ_base[inst];
+  const int64_t lbase = S.icb[inst] < S.icb[inst + 1] ? S.cb[S.icb[inst]] : 0;
+  w.ent = S.ent + lbase;
+  w.head = 0;
+  w.nd = 0;
+  w.nd_fixed = 0;
+  w.inc = job ? job->inc : 1.0f;  // a cube starts from its donor's activities
+  const uint32_t nwords = (w.V + 15u) >> 4;
+  for (uint32_t k = w.lane; k < nwords; k += 32) w.asg[k] = 0u;
+  for (uint32_t v = w.lane; v < w.V; v += 32) {
+    if (!job) w.act[v] = 0.0f;
+    cd.stamp[v] = STAMP_OPEN;
+    cd.mark[v] = 0;
+  }
+  clear_learnts(w, cd);
+  if (w.lane == 0) {
+    w.ws->tail = 0;
+    w.ws->conflict = 0;
+  }
+  __syncwarp();
+  if (S.flags[inst] & F_EMPTY) return SCUBA_UNSAT;
+  const uint64_t no_reason = ~0ull;
+  const uint32_t nu = S.nunits[inst];
+  const uint32_t* un = S.units + w.c0;
+  for (uint32_t k = w.lane; k < nu; k += 32)
+    if (!imply_cd(w, cd, un[k], no_reason)) record_conflict(w, un[k], NONE, NONE);
+  __syncwarp();
+  if (w.ws->conflict) return SCUBA_UNSAT;
+  if (job) {  // the cube's literals as decisions of levels 1, 2, ...
+    for (int k = 0; k < job->len; k++) {
+      if (bcp_cd(w, cd)) return SCUBA_UNSAT;
+      const uint32_t l = job->lit[k];
+      const uint32_t val = lit_value(w.asg, l);
+      if (val == LV_F) return SCUBA_UNSAT;
+      if (val == LV_T) continue;
+      if (w.lane == 0) w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
+      w.nd++;
+      if (w.lane == 0) imply_cd(w, cd, l, no_reason);
+      __syncwarp();
+    }
+    w.nd_fixed = w.nd;
+  }
+
+  uint32_t iter = 0, conflicts = 0, since_restart = 0, restart_no = 1;
+  uint32_t next_reduce = 2000u, reductions = 0;  // periodic database reduction
+  uint32_t restart_at = (uint32_t)S.restart_unit * luby_cd(1);
+  for (;;) {
+    if ((++iter & 63u) == 0u) {
+      int stop = 0;
+      if (w.lane == 0) {
+        if (S.abort_flag && *S.abort_flag) stop = 1;
+        else if (globaltimer() - S.ctrl->t0 > S.time_ns) stop = 2;
+        else if (*(volatile uint32_t*)&S.done[inst] & 1u) stop = 3;
+      }
+      stop = __shfl_sync(FULL, stop, 0);
+      if (stop == 1) { abort_code = SCUBA_ERR_ABORTED; return SCUBA_UNKNOWN; }
+      if (stop == 2) { abort_code = SCUBA_ERR_TIMEOUT; return SCUBA_UNKNOWN; }
+      if (stop == 3) return SCUBA_UNSAT;  // the instance is SAT already; this cube is moot
+      if (cd.round > 0xfffff000u) return SCUBA_UNKNOWN;
+    }
+    long long t0 = pf_now(S);
+    const bool confl = bcp_cd(w, cd);
+    pf_add(S, w, PF_BCP, t0);
+    if (cd.full) {  // the watch pool ran out: compact it (or halve the clauses)
+      maintain_db(w, cd, false);
+      continue;
+    }
+    if (confl) {
+      WCOUNT(w, conflicts, 1);
+      if (w.nd <= w.nd_fixed) return SCUBA_UNSAT;
+      conflicts++;
+      since_restart++;
+      t0 = pf_now(S);
+      uint32_t blev, lbd;
+      const uint32_t n = analyze_cd(w, cd, blev, lbd);
+      if (n == 0) {
+        abort_code = SCUBA_ERR_INTERNAL;
+        return SCUBA_UNKNOWN;
+      }
+      w.inc *= (1.0f / 0.95f);
+      if (w.lane == 0) w.ws->conflict = 0;
+      const uint32_t target = max(blev, w.nd_fixed);
+      if (n >= 2 && (uint64_t)cd.top + clause_words(n) > cd.arena_words) {
+        maintain_db(w, cd, true);  // arena full: restart with half the clauses
+        if ((uint64_t)cd.top + clause_words(n) > cd.arena_words) clear_learnts(w, cd);
+        since_restart = 0;
+      } else {
+        backjump_cd(w, cd, target);
+      }
+      uint64_t why = no_reason;
+      if (n >= 2) {
+        uint32_t c = add_learnt(w, cd, n, lbd);
+        if (cd.full) {  // the pool ran out: compact it, the new clause included
+          maintain_db(w, cd, false);
+          // the newest clause survives a compaction or a halving; after a
+          // full drop it is added again to the empty database
+          c = cd.ncl > 0 ? cd.cl_off[cd.ncl - 1] : add_learnt(w, cd, n, lbd);
+        }
+        why = (uint64_t)(LEARNT_REF | c);
+      }
+      // the clause is unit once every literal but the first is false
+      if (n == 1 || blev <= w.nd) {
+        if (w.lane == 0) imply_cd(w, cd, cd.learnt[0], why);
+        __syncwarp();
+      }
+      pf_add(S, w, PF_ANALYZE, t0);
+      if (S.budget > 0) {  // conflicts of the instance, all of its cubes together
+        unsigned long long tot = 0;
+        if (w.lane == 0) tot = atomicAdd(&S.inst_dec[inst], 1ull) + 1ull;
+        tot = __shfl_sync(FULL, tot, 0);
+        if ((int64_t)tot >= S.budget) return SCUBA_UNKNOWN;
+      }
+      continue;
+    }
+    if (since_restart >= restart_at) {
+      since_restart = 0;
+      restart_no++;
+      restart_at = (uint32_t)S.restart_unit * luby_cd(restart_no);
+      if (conflicts >= next_reduce) {  // a restart that also halves the database
+        reductions++;
+        next_reduce = conflicts + 2000u + 300u * reductions;
+        maintain_db(w, cd, true);
+      } else {
+        backjump_cd(w, cd, w.nd_fixed);
+      }
+      continue;
+    }
+    WCOUNT(w, act_reads, w.V - *(volatile uint32_t*)&w.ws->tail);
+    t0 = pf_now(S);
+    const uint32_t v = pick(w);
+    pf_add(S, w, PF_DECIDE, t0);
+    if (v == NONE) {
+      // the first cube of the instance to reach a model writes it
+      uint32_t won = 0;
+      if (w.lane == 0) won = !(atomicOr(&S.done[inst], 8u) & 8u);
+      won = __shfl_sync(FULL, won, 0);
+      if (won && S.model)
+        for (uint32_t x = w.lane; x < w.V; x += 32) {
+          const uint32_t bits = (w.asg[x >> 4] >> ((x & 15u) * 2u)) & 3u;
+          S.model[S.vb[inst] + x] = bits == 1u ? 1 : 0;
+        }
+      __syncwarp();
+      return SCUBA_SAT;
+    }
+    // cube-and-conquer: hand the other side of the first free decision to an
+    // idle warp and keep this side as an assumption
+    if (S.split && w.decisions >= (uint32_t)S.split_min &&
+        (w.decisions % (uint32_t)S.split_interval) == 0 && w.nd > w.nd_fixed &&
+        w.nd_fixed + 1 <= (uint32_t)MAX_PREFIX) {
+      uint32_t idle = 0;
+      if (w.lane == 0) idle = *(volatile uint32_t*)&S.ctrl->idle;
+      idle = __shfl_sync(FULL, idle, 0);
+      if (idle > 0) {
+        const uint32_t k = w.nd_fixed;
+        if (w.lane == 0) atomicAdd(&S.pending[inst], 1u);
+        __syncwarp();
+        if (ring_push(S, w, inst, k + 1, w.trail, w.dstack, k)) {
+          w.nd_fixed = k + 1;
+          if (w.lane == 0) {
+            atomicAdd(&S.ctrl->jobs_split, 1u);
+            if (S.prof) {
+              atomicAdd(&S.prof[0], 1ull);
+              atomicAdd(&S.prof[2], (unsigned long long)(k + 1));
+              atomicAdd(&S.prof[3], (unsigned long long)(w.nd - k));
+            }
+          }
+        } else if (w.lane == 0) {
+          atomicSub(&S.pending[inst], 1u);
+          if (S.prof) atomicAdd(&S.prof[4], 1ull);
+        }
+        __syncwarp();
+      }
+    }
+    w.decisions++;
+    WCOUNT(w, decisions, 1);
+    const uint32_t lit = 2u * v + ((cd.mark[v] & MK_PHASE) ? 0u : 1u);
+    if (w.lane == 0) w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
+    w.nd++;
+    if (w.lane == 0) imply_cd(w, cd, lit, no_reason);
+    __syncwarp();
+  }
+}

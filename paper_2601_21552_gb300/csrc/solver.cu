@@ -350,7 +350,9 @@ struct TraceDev {
   int32_t* var;                // [max_rows]
 };
 
-enum { MODE_PLAIN = 0, MODE_TRACE = 1, MODE_LEARNED = 2 };
+enum { MODE_PLAIN = 0, MODE_TRACE = 1, MODE_LEARNED = 2, MODE_CDCL = 3 };
+
+struct WList;  // a learned watch list (clause-learning mode)
 
 struct Solve {
   int n;
@@ -402,6 +404,18 @@ struct Solve {
   TraceDev tr;
   uint32_t* lvlcnt;            // [slots][MAX_TRACE_DEPTH][vmax] conflict counts
   int64_t* lvl_node;           // [slots][MAX_TRACE_DEPTH] node of each open level
+  // conflict-driven clause learning (per slot)
+  uint64_t* cd_reason;         // [slots][vmax]
+  uint32_t* cd_level;          // [slots][vmax]
+  uint32_t* cd_stamp;          // [slots][vmax]
+  uint8_t* cd_mark;            // [slots][vmax]
+  WList* cd_wl;                // [slots][2 vmax] learned watch lists
+  uint64_t* cd_pool;           // [slots][cd_pool_cap] watch entries
+  uint32_t* cd_learnt;         // [slots][vmax]
+  uint32_t* cd_arena;          // [slots][cd_arena_words]
+  uint32_t* cd_clidx;          // [slots][cd_arena_words / 8] clause offsets
+  int64_t cd_arena_words, cd_pool_cap;
+  int restart_unit;            // conflicts per Luby unit
 };
 
 struct WarpShared {
@@ -411,6 +425,8 @@ struct WarpShared {
   uint32_t pad[3];
   // per-job work counters (lane 0 updates them; kept out of registers)
   unsigned long long decisions, conflicts, props, visits, act_reads, undone;
+  // clause-learning profile (cycles of lane 0 per phase; counts)
+  unsigned long long cyc[8];
 };
 
 enum : uint32_t { LV_U = 0, LV_T = 1, LV_F = 2, LV_X = 3 };
@@ -527,14 +543,20 @@ __device__ __forceinline__ void eval_entry(Warp& w, uint32_t f, uint64_t e) {
 
 // Unit propagation to a fixpoint. Returns true on conflict.
 // Each round takes the trail literals assigned in the previous round (the
-// frontier) and spreads their occurrence entries over the 32 lanes.
-__device__ bool bcp(Warp& w) {
+// frontier) and spreads their occurrence entries over the 32 lanes:
+// visit(f, entry) evaluates one occurrence entry of the falsified literal f;
+// on_round() runs at the start of each round and after_batch(base, count)
+// after each batch of up to 32 frontier literals (all lanes, both).
+template <class Visit, class Round, class Batch>
+__device__ __forceinline__ bool bcp_rounds(Warp& w, Visit&& visit, Round&& on_round,
+                                           Batch&& after_batch) {
   for (;;) {
     __syncwarp();
     const uint32_t hi = *(volatile uint32_t*)&w.ws->tail;
     if (w.head >= hi) return false;
     const uint32_t lo = w.head;
     w.head = hi;
+    on_round();
     WCOUNT(w, props, hi - lo);
     for (uint32_t base = lo; base < hi; base += 32) {
       const uint32_t nlit = min(32u, hi - base);
@@ -544,7 +566,7 @@ __device__ bool bcp(Warp& w) {
         const uint32_t beg = __ldg(&w.occ[f]);
         const uint32_t cnt = __ldg(&w.occ[f + 1]) - beg;
         WCOUNT(w, visits, cnt);
-        for (uint32_t e = w.lane; e < cnt; e += 32) eval_entry(w, f, __ldg(&w.ent[beg + e]));
+        for (uint32_t e = w.lane; e < cnt; e += 32) visit(f, __ldg(&w.ent[beg + e]));
       } else {
         uint32_t f = 0, beg = 0, cnt = 0;
         if (w.lane < nlit) {
@@ -576,7 +598,7 @@ __device__ bool bcp(Warp& w) {
           const uint32_t jbeg = __shfl_sync(FULL, beg, j);
           const uint32_t jex = __shfl_sync(FULL, excl, j);
           const uint32_t jf = __shfl_sync(FULL, f, j);
-          if (e < total) eval_entry(w, jf, __ldg(&w.ent[jbeg + (e - jex)]));
+          if (e < total) visit(jf, __ldg(&w.ent[jbeg + (e - jex)]));
         } else {
           for (uint32_t e0 = 0; e0 < total; e0 += 32) {
             const uint32_t e = e0 + w.lane;
@@ -593,14 +615,21 @@ __device__ bool bcp(Warp& w) {
             const uint32_t jbeg = __shfl_sync(FULL, beg, j);
             const uint32_t jex = __shfl_sync(FULL, excl, j);
             const uint32_t jf = __shfl_sync(FULL, f, j);
-            if (e < total) eval_entry(w, jf, __ldg(&w.ent[jbeg + (e - jex)]));
+            if (e < total) visit(jf, __ldg(&w.ent[jbeg + (e - jex)]));
           }
         }
       }
+      after_batch(base, nlit);
       __syncwarp();
       if (*(volatile uint32_t*)&w.ws->conflict) return true;
     }
   }
+}
+
+__device__ bool bcp(Warp& w) {
+  return bcp_rounds(
+      w, [&](uint32_t f, uint64_t e) { eval_entry(w, f, e); }, [] {},
+      [](uint32_t, uint32_t) {});
 }
 
 template <int MODE>
@@ -983,7 +1012,11 @@ __device__ void finish_job(const Solve& S, Warp& w, int inst, int r) {
       atomicSub(&S.ctrl->inst_left, 1u);
       if (S.finish_ns) S.finish_ns[inst] = (int64_t)(globaltimer() - S.ctrl->t0);
     }
-    if (S.prof) atomicAdd(&S.prof[1], 1ull);  // jobs run
+    if (S.prof) {
+      atomicAdd(&S.prof[1], 1ull);  // jobs run
+      for (int k = 0; k < 8; k++)
+        if (w.ws->cyc[k]) atomicAdd(&S.prof[8 + k], w.ws->cyc[k]);
+    }
     if (S.stats) {
       unsigned long long* st = (unsigned long long*)&S.stats[SCUBA_NSTATS * (int64_t)inst];
       atomicAdd(st + 0, w.ws->decisions);
@@ -1158,15 +1191,24 @@ __device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* j
   }
 }
 
+#include "cdcl.cuh"
+
 // Plain search: 48 registers per thread, 5 blocks x 8 warps = 40 resident
 // warps per SM. The learned variant (MLP on the tensor cores) defaults to 4
 // blocks (64 registers); SCUBA_LEARNED_MINBLOCKS=5 trades spills for warps
-// (measured slower).
+// (measured slower). The clause-learning variant runs 2 blocks (116
+// registers, no spills): measured faster than 3 (80 registers) or 4 (64,
+// spilling) on partition queries and on random 3-SAT.
 #ifndef SCUBA_LEARNED_MINBLOCKS
 #define SCUBA_LEARNED_MINBLOCKS 4
 #endif
+#ifndef SCUBA_CDCL_MINBLOCKS
+#define SCUBA_CDCL_MINBLOCKS 2
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINBLOCKS : 5)
+__global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINBLOCKS
+                                       : MODE == MODE_CDCL  ? SCUBA_CDCL_MINBLOCKS
+                                                            : 5)
     k_solve(const __grid_constant__ Solve S) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31;
@@ -1262,6 +1304,7 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
     if (lane == 0) {
       w.ws->decisions = w.ws->conflicts = w.ws->props = 0;
       w.ws->visits = w.ws->act_reads = w.ws->undone = 0;
+      for (int k = 0; k < 8; k++) w.ws->cyc[k] = 0;
     }
     __syncwarp();
     uint32_t moot = 0;
@@ -1275,6 +1318,8 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
       if (lane == 0) set_status(S, SCUBA_ERR_TOO_LARGE);
     } else if (moot) {
       r = SCUBA_UNSAT;  // moot: another subtree already found a model
+    } else if constexpr (MODE == MODE_CDCL) {
+      r = run_cdcl(S, w, slot, inst, job, abort_code);
     } else {
       r = run_job<MODE>(S, w, inst, job, abort_code);
     }
@@ -1415,10 +1460,11 @@ struct Scratch {
   Buf occ_base, norm, occ_cnt, occ_begin, ent, units, nunits, flags;
   Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
   Buf lvlcnt, lvl_node;
+  Buf cd_reason, cd_level, cd_stamp, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
   int32_t last_status = 0;
-  int smem_set[3] = {0, 0, 0};  // dynamic shared memory granted per search mode
+  int smem_set[4] = {0, 0, 0, 0};  // dynamic shared memory granted per search mode
   int smem_prop = 0;
 };
 
@@ -1504,6 +1550,17 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
     set_error("scuba_solve_batch: unknown heuristic");
     return SCUBA_ERR_ARG;
   }
+  if (opt->search != SCUBA_SEARCH_DPLL && opt->search != SCUBA_SEARCH_CDCL) {
+    set_error("scuba_solve_batch: unknown search algorithm");
+    return SCUBA_ERR_ARG;
+  }
+  if (opt->search == SCUBA_SEARCH_CDCL &&
+      (opt->trace || opt->heuristic != SCUBA_HEUR_ACTIVITY || opt->restart_unit < 0 ||
+       opt->learnt_words < 0 || opt->learnt_words >= (1LL << 30))) {
+    set_error("scuba_solve_batch: CDCL takes activity branching, no trace, restart_unit >= 0 "
+              "and 0 <= learnt_words < 2^30");
+    return SCUBA_ERR_ARG;
+  }
   if (b->max_vars >= (1 << 29)) {
     set_error("scuba_solve_batch: instance too large (max_vars >= 2^29)");
     return SCUBA_ERR_TOO_LARGE;
@@ -1524,6 +1581,8 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
       return SCUBA_ERR_ARG;
     }
     mode = dev::MODE_LEARNED;
+  } else if (opt->search == SCUBA_SEARCH_CDCL) {
+    mode = dev::MODE_CDCL;
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1564,6 +1623,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   }
   while (bps > 1 && (smem + 1024) * bps > sm_cap) bps--;
   if (mode == dev::MODE_LEARNED) bps = std::min(bps, SCUBA_LEARNED_MINBLOCKS);
+  if (mode == dev::MODE_CDCL) bps = std::min(bps, SCUBA_CDCL_MINBLOCKS);
   const int64_t slots = (int64_t)S.sms * bps * wpb;
   const uint32_t ring_cap = 2048;
 
@@ -1585,6 +1645,26 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
        ensure(S.lvl_node, 8 * (size_t)slots * learn::MAX_TRACE_DEPTH))) {
     set_error("scuba_solve_batch: out of device memory for trace scratch");
     return SCUBA_ERR_NOMEM;
+  }
+  int64_t arena_words = 0;
+  if (mode == dev::MODE_CDCL) {
+    arena_words = (opt->learnt_words > 0 ? opt->learnt_words : (1LL << 18)) & ~3LL;
+    if (arena_words < std::max<int64_t>((int64_t)vmax + 2 * dev::CD_HDR, 64)) {
+      set_error("scuba_solve_batch: learnt_words must be at least max(max_vars + 8, 64)");
+      return SCUBA_ERR_ARG;
+    }
+    if (ensure(S.cd_reason, 8 * (size_t)slots * vmax) ||
+        ensure(S.cd_level, 4 * (size_t)slots * vmax) ||
+        ensure(S.cd_stamp, 4 * (size_t)slots * vmax) ||
+        ensure(S.cd_mark, (size_t)slots * vmax) ||
+        ensure(S.cd_wl, 32 * (size_t)slots * vmax) ||
+        ensure(S.cd_pool, 8 * (size_t)slots * arena_words) ||
+        ensure(S.cd_learnt, 4 * (size_t)slots * vmax) ||
+        ensure(S.cd_arena, 4 * (size_t)slots * arena_words) ||
+        ensure(S.cd_clidx, 4 * (size_t)slots * (arena_words / 8))) {
+      set_error("scuba_solve_batch: out of device memory for clause-learning scratch");
+      return SCUBA_ERR_NOMEM;
+    }
   }
   dev::Prep pr;
   pr.n = n;
@@ -1666,6 +1746,18 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.trace_depth = 0;
   sv.lvlcnt = nullptr;
   sv.lvl_node = nullptr;
+  sv.cd_reason = P<uint64_t>(S.cd_reason);
+  sv.cd_level = P<uint32_t>(S.cd_level);
+  sv.cd_stamp = P<uint32_t>(S.cd_stamp);
+  sv.cd_mark = P<uint8_t>(S.cd_mark);
+  sv.cd_wl = P<dev::WList>(S.cd_wl);
+  sv.cd_pool = P<uint64_t>(S.cd_pool);
+  sv.cd_pool_cap = arena_words;
+  sv.cd_learnt = P<uint32_t>(S.cd_learnt);
+  sv.cd_arena = P<uint32_t>(S.cd_arena);
+  sv.cd_clidx = P<uint32_t>(S.cd_clidx);
+  sv.cd_arena_words = arena_words;
+  sv.restart_unit = opt->restart_unit > 0 ? opt->restart_unit : 100;
   std::memset(&sv.tr, 0, sizeof(sv.tr));
   if (mode == dev::MODE_TRACE) {
     const scuba_trace* T = opt->trace;
@@ -1693,6 +1785,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   dev::k_start_clock<<<1, 1, 0, st>>>(sv.ctrl);
   auto kern = mode == dev::MODE_TRACE     ? dev::k_solve<dev::MODE_TRACE>
               : mode == dev::MODE_LEARNED ? dev::k_solve<dev::MODE_LEARNED>
+              : mode == dev::MODE_CDCL    ? dev::k_solve<dev::MODE_CDCL>
                                           : dev::k_solve<dev::MODE_PLAIN>;
   // raise the dynamic shared-memory limit only when it grows, so that a
   // repeated call (for example while a CUDA graph is being captured) issues
@@ -1791,7 +1884,10 @@ extern "C" void scuba_release(void) {
   Scratch& S = it->second;
   Buf* all[] = {&S.occ_base, &S.norm, &S.occ_cnt, &S.occ_begin, &S.ent, &S.units, &S.nunits,
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
-                &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node, &S.h_icb, &S.h_cb, &S.h_lits, &S.h_nv, &S.h_vb,
+                &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node,
+                &S.cd_reason, &S.cd_level, &S.cd_stamp, &S.cd_mark, &S.cd_wl, &S.cd_pool,
+                &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.h_icb, &S.h_cb, &S.h_lits,
+                &S.h_nv, &S.h_vb,
                 &S.h_verdict, &S.h_model, &S.h_stats};
   for (Buf* x : all) {
     if (x->p) cudaFree(x->p);
@@ -1844,8 +1940,8 @@ extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verd
     set_error("scuba_solve_batch_noalloc: NULL array");
     return SCUBA_ERR_ARG;
   }
-  if (opt->heuristic != SCUBA_HEUR_ACTIVITY) {
-    set_error("scuba_solve_batch_noalloc: only activity branching is supported");
+  if (opt->heuristic != SCUBA_HEUR_ACTIVITY || opt->search != SCUBA_SEARCH_DPLL) {
+    set_error("scuba_solve_batch_noalloc: only DPLL with activity branching is supported");
     return SCUBA_ERR_ARG;
   }
   if (b->max_vars >= (1 << 29) || b->total_lits >= (1LL << 32)) {
