@@ -5,17 +5,19 @@ the partition/bounds family shaped like the paper's Figs. 1, 3 and 5 (seeded
 synthetic inputs; the paper's 20 programs are not available). One step = one
 complete pass of the hot path over the batch with the CNFs already resident
 in HBM: device prep (clause normalisation, occurrence lists) + the
-persistent DPLL search + verdict finalisation. Verdicts are checked
-bit-exactly against stored oracle verdicts after timing.
+persistent search + verdict finalisation. Verdicts are checked bit-exactly
+against stored oracle verdicts after timing.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--heuristic plain|learned|both]
+                    [--arms cdcl,learned,plain]
 
-The headline value is the learned arm: the incidence MLP, trained beforehand
-(not timed as a step; reported under "learned_training") on decision traces
-of the plain search over held-out seeds, orders the top decisions; the plain
-arm (activity branching only) is reported beside it under "arms". Both arms
-must return identical verdicts, bit-exact against the stored oracle verdicts.
+Arms (each a full pass over the same batch, same verdicts required):
+  cdcl     conflict-driven clause learning with activity branching (headline)
+  learned  DPLL whose top decisions are ordered by the incidence MLP, trained
+           beforehand (not timed; reported under "learned_training") on
+           decision traces of the plain search over held-out seeds
+  plain    DPLL with activity branching only
+The headline value is the first arm; all arms are reported under "arms".
 
 Under torchrun each rank solves its own batch (different seeds): weak
 scaling, no collective on the data path.
@@ -152,9 +154,9 @@ def _stored_verdicts():
     return np.array([int(x) for x in open(p).read().split()], np.uint8)
 
 
-def cpu_baseline(irs, target_s: float = 15.0, seed: int = 7):
+def cpu_baseline(irs, target_s: float = 15.0, seed: int = 7, algo: str = "cdcl"):
     """The oracle as it stands, on a bounded random sample of the workload,
-    on all host cores."""
+    on all host cores (algo: its clause-learning or its DPLL solver)."""
     import oracle
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(irs))
@@ -165,35 +167,35 @@ def cpu_baseline(irs, target_s: float = 15.0, seed: int = 7):
     while t_used < target_s and k < len(order):
         sel = [irs[i] for i in order[k:k + chunk]]
         t0 = time.perf_counter()
-        r = oracle.solve_queries(sel, threads=threads)
+        r = oracle.solve_queries(sel, threads=threads, algo=algo)
         t_used += time.perf_counter() - t0
         done += len(sel)
         props += int(r["stats"][:, 2].sum())
         k += chunk
     return {"value": done / t_used, "unit": "verdicts/s", "cores": threads, "kind": "oracle",
+            "algo": algo,
             "sample": f"{done} of {len(irs)} queries drawn uniformly (seed {seed}), {t_used:.1f}s",
             "propagations_per_s": props / t_used}
 
 
 def run_reference(args):
+    """The oracle on the host cores: its clause-learning solver over the whole
+    4,096-query workload per step (the DPLL solver would need minutes per
+    step; it is timed on a sample inside the GPU arm's cpu_baseline_dpll)."""
     ws, rank = _dist()
     if rank != 0:
         return
     import oracle
     irs, _ = _workload(0, 4096)
-    rng = np.random.default_rng(11)
     threads = oracle.default_threads()
-    per_step = 96
     times, counts, props = [], [], []
     for s in range(args.warmup + args.steps):
-        sel_idx = rng.choice(len(irs), size=per_step, replace=False)
-        sel = [irs[i] for i in sel_idx]
         t0 = time.perf_counter()
-        r = oracle.solve_queries(sel, threads=threads)
+        r = oracle.solve_queries(irs, threads=threads, algo="cdcl")
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
-            counts.append(len(sel))
+            counts.append(len(irs))
             props.append(int(r["stats"][:, 2].sum()))
     tot = sum(times)
     value = sum(counts) / tot
@@ -201,12 +203,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_per_step": per_step,
+            "config": {"workload": WORKLOAD, "queries_per_step": len(irs),
                        "propagations_per_s": sum(props) / tot},
-            "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value,
+            "cpu_baseline": {"kind": "oracle", "algo": "cdcl", "cores": threads, "value": value,
                              "unit": "verdicts/s",
-                             "sample": f"{per_step} queries per step drawn uniformly from the "
-                                       f"4,096-query workload"},
+                             "sample": "the whole 4,096-query workload every step"},
             "e2e": {"value": value, "unit": "verdicts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -313,23 +314,29 @@ def run_ours(args):
 
     from paper_2601_21552_gb300 import autotune
     tuned = autotune.load()  # launch shape / sharing parameters from the last sweep
-    # learned first: it is the headline (the learned-branching batched form);
-    # plain activity branching is measured beside it as the method without it
-    arms = ["learned", "plain"] if args.heuristic == "both" else [args.heuristic]
+    tuned_cdcl = autotune.load(section="best_cdcl")
+    # the first arm is the headline; the others are measured beside it
+    arms = [a for a in args.arms.split(",") if a]
+    assert arms and set(arms) <= {"cdcl", "learned", "plain"}, args.arms
     net, train_info = None, None
     if "learned" in arms:
         net, train_info = _train_network(api, B, dev, args)
+
+    def arm_options(arm):
+        opts = dict(tuned)
+        if arm == "learned":
+            opts.update(heuristic=B.SCUBA_HEUR_LEARNED, mlp_weights=net.weights,
+                        learned_depth=args.learned_depth)
+        elif arm == "cdcl":
+            opts.update(tuned_cdcl, search="cdcl")
+        return opts
 
     if ws > 1:
         torch.distributed.barrier()
     results = {}
     with ClockSampler(local) as clk:
         for arm in arms:
-            opts = dict(tuned)
-            if arm == "learned":
-                opts.update(heuristic=B.SCUBA_HEUR_LEARNED, mlp_weights=net.weights,
-                            learned_depth=args.learned_depth)
-            results[arm] = _timed_arm(api, B, db, dev, stream, count, opts, args,
+            results[arm] = _timed_arm(api, B, db, dev, stream, count, arm_options(arm), args,
                                       use_graph=args.graph)
     if ws > 1:
         torch.distributed.barrier()
@@ -344,8 +351,8 @@ def run_ours(args):
             ok = int((results[arm]["verdict"] == stored).sum())
             assert ok == count, f"{arm}: verdicts differ from the oracle on {count - ok} queries"
             parity[arm] = f"{ok}/{count} bit-exact"
-    if len(arms) == 2:
-        assert (results["plain"]["verdict"] == results["learned"]["verdict"]).all()
+    for arm in arms[1:]:
+        assert (results[arm]["verdict"] == results[arms[0]]["verdict"]).all(), arm
 
     # end to end through the host entry point (host buffers, copies inside)
     h_verdict = np.zeros(count, np.uint8)
@@ -353,7 +360,7 @@ def run_ours(args):
                       enc.inst_clause_begin.ctypes.data, enc.clause_begin.ctypes.data,
                       enc.lits.ctypes.data, enc.inst_num_vars.ctypes.data,
                       enc.inst_var_begin.ctypes.data)
-    o = api.options(time_budget_ms=300000)
+    o = api.options(time_budget_ms=300000, **arm_options(arms[0]))  # the headline arm
     B.scuba_solve_batch_host(hb, h_verdict, None, stream.cuda_stream, o)  # warm
     e2e_t = []
     for _ in range(max(1, min(args.steps, 3))):
@@ -395,7 +402,9 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "heuristic": arms[0],
+        "arm": arms[0],
+        "search": "cdcl" if arms[0] == "cdcl" else "dpll",
+        "heuristic": "learned" if arms[0] == "learned" else "activity",
         "propagations_per_s": head["propagations_per_s"],
         "config": {"workload": WORKLOAD, "queries_per_gpu": count, "input_bits": args.width,
                    "clauses_total": enc.total_clauses, "literals_total": enc.total_lits,
@@ -421,7 +430,10 @@ def run_ours(args):
     if train_info:
         line["learned_training"] = train_info
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(irs, target_s=args.cpu_seconds)
+        # the oracle's clause-learning solver (the stronger CPU program), and
+        # its DPLL beside it
+        line["cpu_baseline"] = cpu_baseline(irs, target_s=args.cpu_seconds, algo="cdcl")
+        line["cpu_baseline_dpll"] = cpu_baseline(irs, target_s=args.cpu_seconds / 2, algo="dpll")
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -433,7 +445,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--heuristic", default="both", choices=["plain", "learned", "both"])
+    ap.add_argument("--arms", default="cdcl,learned,plain",
+                    help="comma list of cdcl, learned, plain; the first is the headline")
     ap.add_argument("--graph", action="store_true",
                     help="replay each step from a captured CUDA graph")
     ap.add_argument("--learned-depth", type=int, default=6,

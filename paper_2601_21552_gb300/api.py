@@ -167,7 +167,10 @@ def solve(db: DeviceBatch, want_model: bool = True, stats: bool = True,
     dev = db.icb.device
     if opts.pop("tuned", False):
         from . import autotune
-        for k, v in autotune.load().items():
+        tuned = autotune.load()
+        if opts.get("search") == "cdcl":
+            tuned.update(autotune.load(section="best_cdcl"))
+        for k, v in tuned.items():
             opts.setdefault(k, v)
     if opts.get("order") == "lpt":
         opts["order"] = db.lpt_order()

@@ -47,7 +47,9 @@ def _report(name, d):
             json.dump(d, f)
 
 
-def test_uneven_batch_65536(libs):
+@pytest.mark.parametrize("search", ["dpll", "cdcl"])
+def test_uneven_batch_65536(libs, search):
+    """With DPLL the budget counts decisions, with clause learning conflicts."""
     api, B = libs
     t0 = time.perf_counter()
     irs, meta = queries.config3(65536)
@@ -60,7 +62,8 @@ def test_uneven_batch_65536(libs):
     torch.cuda.synchronize()
     budget = 100_000
     t0 = time.perf_counter()
-    v, m, st = api.solve(db, order="lpt", decision_budget=budget, time_budget_ms=600000)
+    v, m, st = api.solve(db, order="lpt", decision_budget=budget, time_budget_ms=600000,
+                         search=search, tuned=True)
     rc = api.status()
     t_solve = time.perf_counter() - t0
     assert rc == 0, B.last_error()
@@ -73,13 +76,14 @@ def test_uneven_batch_65536(libs):
     small = np.argsort(nc, kind="stable")[:64]
     mid = rng.choice(np.flatnonzero(nc < 20000), 64, replace=False)
     sample = np.unique(np.concatenate([small, mid]))
-    ref = oracle.solve_queries([irs[i] for i in sample], budget=300000)["verdict"]
+    ref = oracle.solve_queries([irs[i] for i in sample], budget=300000, algo=search)["verdict"]
     both = (ref != 2) & (vh[sample] != 2)
     assert (ref[both] == vh[sample][both]).all()
     w = np.array([x["w"] for x in meta])
     rep = {"queries": 65536, "clauses_total": int(enc.total_clauses),
            "literals_total": int(enc.total_lits), "clauses_p50": int(np.median(nc)),
-           "clauses_max": int(nc.max()), "decision_budget": budget,
+           "clauses_max": int(nc.max()), "search": search, "budget": budget,
+           "budget_counts": "conflicts" if search == "cdcl" else "decisions",
            "sat": int((vh == 1).sum()), "unsat": int((vh == 0).sum()),
            "unknown": int((vh == 2).sum()),
            "unknown_by_width": {str(x): int(((vh == 2) & (w == x)).sum()) for x in (8, 16, 32)},
@@ -87,7 +91,7 @@ def test_uneven_batch_65536(libs):
            "verdicts_per_s": 65536 / t_solve,
            "propagations_per_s": float(sth[:, 2].sum()) / t_solve,
            "oracle_sample": int(len(sample)), "oracle_sample_both_decided": int(both.sum())}
-    _report("uneven_65536", rep)
+    _report("uneven_65536" + ("_cdcl" if search == "cdcl" else ""), rep)
 
 
 def _pack_mixed(sat, enc):
@@ -111,7 +115,8 @@ def _pack_mixed(sat, enc):
     return icb, np.concatenate(cb), np.concatenate(lits).astype(np.int32), nv, vb
 
 
-def test_bcp_stress_mixed_batch(libs):
+@pytest.mark.parametrize("search", ["dpll", "cdcl"])
+def test_bcp_stress_mixed_batch(libs, search):
     api, B = libs
     sat = queries.config5_sat(10000)
     b_irs, b_params = queries.config5_bounds(10000)
@@ -121,7 +126,8 @@ def test_bcp_stress_mixed_batch(libs):
     torch.cuda.synchronize()
     budget = 200_000
     t0 = time.perf_counter()
-    v, m, st = api.solve(db, decision_budget=budget, time_budget_ms=600000)
+    v, m, st = api.solve(db, decision_budget=budget, time_budget_ms=600000, search=search,
+                         tuned=True)
     rc = api.status()
     t_solve = time.perf_counter() - t0
     assert rc == 0, B.last_error()
@@ -143,11 +149,11 @@ def test_bcp_stress_mixed_batch(libs):
     idx = np.random.default_rng(1).choice(10000, 200, replace=False)
     ocnf = [oracle.CNF(sat[i][0], np.arange(0, 3 * len(sat[i][1]) + 1, 3),
                        sat[i][1].reshape(-1)) for i in idx]
-    ref = oracle.solve_cnfs(ocnf, budget=budget)["verdict"]
+    ref = oracle.solve_cnfs(ocnf, budget=budget, algo=search)["verdict"]
     both = (ref != 2) & (vh[idx] != 2)
     assert (ref[both] == vh[idx][both]).all()
     rep = {"instances": 20000, "random_3sat": 10000, "bounds_32bit": 10000,
-           "decision_budget": budget, "solve_s": t_solve,
+           "search": search, "budget": budget, "solve_s": t_solve,
            "sat_3sat": int((vh[:10000] == 1).sum()), "unsat_3sat": int((vh[:10000] == 0).sum()),
            "unknown_3sat": int((vh[:10000] == 2).sum()),
            "sat_bounds": int((vb_q == 1).sum()), "unsat_bounds": int((vb_q == 0).sum()),
@@ -155,4 +161,4 @@ def test_bcp_stress_mixed_batch(libs):
            "propagations": int(sth[:, 2].sum()),
            "propagations_per_s": float(sth[:, 2].sum()) / t_solve,
            "oracle_sample_both_decided": int(both.sum())}
-    _report("bcp_stress_20000", rep)
+    _report("bcp_stress_20000" + ("_cdcl" if search == "cdcl" else ""), rep)
