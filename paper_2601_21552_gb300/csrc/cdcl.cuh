@@ -6,9 +6,11 @@
 // internally and says no more about it; this mode puts the textbook
 // first-UIP scheme on top of the GPU propagation of the DPLL mode:
 //
-//  * Every assigned variable keeps its reason (the occurrence entry or clause
-//    reference that implied it), its decision level and the BCP round it was
-//    assigned in (stamp).
+//  * The assignment takes 4 bits per variable in shared memory: value (true,
+//    false) and a "fresh" bit, set by the same compare-and-swap that claims
+//    the variable during a BCP round and cleared when the round after it
+//    starts. Every assigned variable keeps its reason (the occurrence entry or
+//    clause reference that implied it) and its decision level.
 //  * Propagation rounds are frontier-parallel, so two lanes can assign
 //    variables of the same round in either trail order. An implication may
 //    therefore only rely on false literals assigned BEFORE the current round;
@@ -59,7 +61,8 @@
 constexpr uint32_t LEARNT_REF = 0xC0000000u;  // clause reference: learned clause at offset
 constexpr uint32_t CD_HDR = 4;
 constexpr uint64_t WATCH_GONE = ~0ull;     // tombstone of a moved watch entry
-constexpr uint32_t STAMP_OPEN = 0xffffffffu;  // stamp of an unassigned variable
+constexpr uint32_t NB_T = 1u, NB_F = 2u, NB_FRESH = 4u;  // assignment nibble bits
+constexpr uint32_t RING = 128;  // recent-trail entries per warp in shared memory
 constexpr uint8_t MK_PHASE = 1, MK_SEEN = 2;
 
 // Profile counters (only when the caller passed a profile array): lane 0
@@ -86,47 +89,63 @@ struct WList {       // one literal's learned watch list in the pool
 struct CdWarp {
   uint64_t* reason;   // [V] occurrence entry {a, b} or clause reference (low word)
   uint32_t* level;    // [V]
-  uint32_t* stamp;    // [V] BCP round of the assignment, STAMP_OPEN when unassigned
   uint8_t* mark;      // [V] MK_PHASE saved phase, MK_SEEN during analysis
   WList* wl;          // [2V] learned watch list per literal code
   uint64_t* pool;     // [pool_cap] watch entries {clause, blocker}
   uint32_t* arena;    // [arena_words]
   uint32_t* cl_off;   // [arena_words / 8] arena offset of each learned clause, oldest first
   uint32_t* learnt;   // [V] clause under construction
+  uint2* ring;        // [RING] shared memory: {literal, trail position} of recent claims
   uint32_t arena_words, pool_cap;
   uint32_t top;       // first free arena word
   uint32_t ncl;       // learned clauses in the arena
   uint32_t pool_top;  // first free pool entry
-  uint32_t round;     // current BCP round
   uint32_t full;      // the pool ran out during propagation: drop the learned clauses
 };
 
-// Assign l with reason `why` at the current level. False on a clash.
-__device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64_t why) {
-  const uint32_t v = l >> 1;
-  const uint32_t sh = (v & 15u) * 2u;
-  const uint32_t mask = ((l & 1u) ? 2u : 1u) << sh;
-  const uint32_t old = atomicOr(&w.asg[v >> 4], mask);
-  const uint32_t ob = (old >> sh) & 3u;
-  if (ob == 0u) {
-    const uint32_t pos = atomicAdd(&w.ws->tail, 1u);
-    w.trail[pos] = l;
-    cd.reason[v] = why;
-    cd.level[v] = w.nd;
-    cd.stamp[v] = cd.round;
-    return true;
-  }
-  if (ob == (mask >> sh)) return true;
-  if ((old & mask) == 0u) atomicAnd(&w.asg[v >> 4], ~mask);
-  return false;
+// The nibble of variable v (value bits and fresh bit).
+__device__ __forceinline__ uint32_t nib(const uint32_t* asg, uint32_t v) {
+  return (asg[v >> 3] >> ((v & 7u) * 4u)) & 7u;
 }
 
-// Was (assigned) literal l set during the current round? An unassigned
-// variable's stamp is STAMP_OPEN, and a variable claimed this round holds
-// STAMP_OPEN or the current round until its claimer's store lands: both read
-// as fresh.
-__device__ __forceinline__ bool fresh(const CdWarp& cd, uint32_t l) {
-  return *(volatile const uint32_t*)&cd.stamp[l >> 1] >= cd.round;
+// Value (LV_U, LV_T, LV_F) of literal l whose variable has nibble n.
+__device__ __forceinline__ uint32_t nib_value(uint32_t n, uint32_t l) {
+  const uint32_t b = n & 3u;
+  if (b == 0u) return LV_U;
+  return ((b == NB_T) != ((l & 1u) != 0u)) ? LV_T : LV_F;
+}
+
+__device__ __forceinline__ uint32_t lit_value_cd(const uint32_t* asg, uint32_t l) {
+  return nib_value(nib(asg, l >> 1), l);
+}
+
+// Assign l with reason `why` at the current level; fresh marks a claim made
+// inside a BCP round. One compare-and-swap claims value and fresh bit
+// together. Returns false on a clash with the opposite value.
+__device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64_t why,
+                                         uint32_t fresh = NB_FRESH) {
+  const uint32_t v = l >> 1, wi = v >> 3, sh = (v & 7u) * 4u;
+  const uint32_t val = (l & 1u) ? NB_F : NB_T;
+  uint32_t old = w.asg[wi];
+  for (;;) {
+    const uint32_t cur = (old >> sh) & 3u;
+    if (cur) return cur == val;
+    const uint32_t prev = atomicCAS(&w.asg[wi], old, old | ((val | fresh) << sh));
+    if (prev == old) break;
+    old = prev;
+  }
+  const uint32_t pos = atomicAdd(&w.ws->tail, 1u);
+  w.trail[pos] = l;
+  cd.ring[pos & (RING - 1u)] = make_uint2(l, pos);
+  cd.reason[v] = why;
+  cd.level[v] = w.nd;
+  return true;
+}
+
+// trail[p], from the shared-memory ring when its slot still holds position p.
+__device__ __forceinline__ uint32_t trail_at(const Warp& w, const CdWarp& cd, uint32_t p) {
+  const uint2 e = cd.ring[p & (RING - 1u)];
+  return e.y == p ? e.x : w.trail[p];
 }
 
 __device__ void eval_long_cd(Warp& w, CdWarp& cd, uint32_t local) {
@@ -134,24 +153,27 @@ __device__ void eval_long_cd(Warp& w, CdWarp& cd, uint32_t local) {
   const int64_t b = w.cb[c], e = w.cb[c + 1];
   uint32_t open_lit = NONE;
   int n_open = 0;
+  bool fresh_false = false;
   for (int64_t q = b; q < e; q++) {
     const uint32_t x = code_of(__ldg(&w.lits[q]));
-    const uint32_t vx = lit_value(w.asg, x);
-    if (vx == LV_T || vx == LV_X) return;
-    if (vx == LV_U && x != open_lit) {
-      n_open++;
-      open_lit = x;
-      if (n_open > 1) return;
+    const uint32_t n = nib(w.asg, x >> 1);
+    const uint32_t vx = nib_value(n, x);
+    if (vx == LV_T) return;
+    if (vx == LV_U) {
+      if (x != open_lit) {
+        n_open++;
+        open_lit = x;
+        if (n_open > 1) return;
+      }
+    } else if (n & NB_FRESH) {
+      fresh_false = true;
     }
   }
   if (n_open == 0) {
     record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
     return;
   }
-  for (int64_t q = b; q < e; q++) {
-    const uint32_t x = code_of(__ldg(&w.lits[q]));
-    if (x != open_lit && fresh(cd, x)) return;  // next round
-  }
+  if (fresh_false) return;  // a literal falsified this round: next round
   if (!imply_cd(w, cd, open_lit, (uint64_t)(LONG_CLAUSE | local)))
     record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
 }
@@ -163,22 +185,24 @@ __device__ __forceinline__ void eval_entry_cd(Warp& w, CdWarp& cd, uint32_t f, u
     eval_long_cd(w, cd, a & ~LONG_CLAUSE);
     return;
   }
-  const uint32_t va = lit_value(w.asg, a);
+  const uint32_t na = nib(w.asg, a >> 1);
+  const uint32_t va = nib_value(na, a);
   if (b == NONE) {  // binary (f | a): a's reason is {f}
-    if (va == LV_T || va == LV_X) return;
+    if (va == LV_T) return;
     if (va == LV_F || !imply_cd(w, cd, a, (uint64_t)f | ((uint64_t)NONE << 32)))
       record_conflict(w, f, a, NONE);
     return;
   }
-  const uint32_t vb = lit_value(w.asg, b);  // ternary (f | a | b)
-  if (va == LV_T || vb == LV_T || va == LV_X || vb == LV_X) return;
+  const uint32_t nb = nib(w.asg, b >> 1);
+  const uint32_t vb = nib_value(nb, b);  // ternary (f | a | b)
+  if (va == LV_T || vb == LV_T) return;
   if (va == LV_F && vb == LV_F) {
     record_conflict(w, f, a, b);
   } else if (va == LV_F) {
-    if (fresh(cd, a)) return;
+    if (na & NB_FRESH) return;  // next round
     if (!imply_cd(w, cd, b, (uint64_t)f | ((uint64_t)a << 32))) record_conflict(w, f, a, b);
   } else if (vb == LV_F) {
-    if (fresh(cd, b)) return;
+    if (nb & NB_FRESH) return;
     if (!imply_cd(w, cd, a, (uint64_t)f | ((uint64_t)b << 32))) record_conflict(w, f, a, b);
   }
 }
@@ -210,24 +234,31 @@ __device__ void wl_append(Warp& w, CdWarp& cd, uint32_t g, uint64_t e) {
   __syncwarp();
 }
 
-// First position >= 2 of a learned clause whose literal passes ok(), NONE if
-// none does. Literals are read 8 at a time (two 16-byte loads; clauses are
-// 16-byte aligned and padded), and the 8 tests are made before the first
-// hit is picked, so that their loads are in flight together.
-template <class Ok>
-__device__ __forceinline__ uint32_t scan_clause(const uint32_t* lits, uint32_t len, Ok&& ok) {
+// A new watch for a learned clause: the first position >= 2 whose literal is
+// not false, else the first whose literal was falsified during this round
+// (its own list brings the clause back next round), else NONE. Literals are
+// read 8 at a time (two 16-byte loads; clauses are 16-byte aligned and
+// padded).
+__device__ __forceinline__ uint32_t new_watch(const uint32_t* asg, const uint32_t* lits,
+                                              uint32_t len) {
   const uint4* L4 = reinterpret_cast<const uint4*>(lits);
+  uint32_t fresh_pos = NONE;
   for (uint32_t q = 0; q < len; q += 8) {
     const uint4 a = L4[q >> 2];
     const uint4 b = q + 4 < len ? L4[(q >> 2) + 1] : make_uint4(NONE, NONE, NONE, NONE);
     const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    uint32_t hit = 0;
+    uint32_t open = 0, fr = 0;
 #pragma unroll
-    for (int i = 0; i < 8; i++)
-      if (q + i >= 2 && q + i < len && ok(x[i])) hit |= 1u << i;
-    if (hit) return q + __ffs(hit) - 1;
+    for (int i = 0; i < 8; i++) {
+      if (q + i < 2 || q + i >= len) continue;
+      const uint32_t n = nib(asg, x[i] >> 1);
+      if (nib_value(n, x[i]) != LV_F) open |= 1u << i;
+      else if (n & NB_FRESH) fr |= 1u << i;
+    }
+    if (open) return q + __ffs(open) - 1;
+    if (fr && fresh_pos == NONE) fresh_pos = q + __ffs(fr) - 1;
   }
-  return NONE;
+  return fresh_pos;
 }
 
 // One watch entry (clause c, blocker) of the falsified literal f, at pool
@@ -239,17 +270,12 @@ __device__ uint32_t visit_learnt(Warp& w, CdWarp& cd, uint32_t f, uint32_t at, u
   const uint32_t l0 = C[CD_HDR], l1 = C[CD_HDR + 1];
   const uint32_t which = l0 == f ? 0u : 1u;
   const uint32_t other = which ? l0 : l1;
-  const uint32_t vo = lit_value(w.asg, other);
+  const uint32_t vo = lit_value_cd(w.asg, other);
   if (vo == LV_T) {
     cd.pool[at] = (uint64_t)c | ((uint64_t)other << 32);  // new blocker
     return NONE;
   }
-  // a new watch among lit2..: first a literal that is not false, else one
-  // falsified during this round (its own list brings the clause back)
-  const uint32_t len = C[0];
-  const uint32_t* lits = C + CD_HDR;
-  uint32_t k = scan_clause(lits, len, [&](uint32_t x) { return lit_value(w.asg, x) != LV_F; });
-  if (k == NONE) k = scan_clause(lits, len, [&](uint32_t x) { return fresh(cd, x); });
+  const uint32_t k = new_watch(w.asg, C + CD_HDR, C[0]);
   if (k != NONE) {
     const uint32_t g = C[CD_HDR + k];
     C[CD_HDR + k] = f;
@@ -263,22 +289,17 @@ __device__ uint32_t visit_learnt(Warp& w, CdWarp& cd, uint32_t f, uint32_t at, u
   } else if (vo == LV_U) {
     if (!imply_cd(w, cd, other, (uint64_t)(LEARNT_REF | c)))
       record_conflict(w, LEARNT_REF | c, NONE, NONE);
-  }  // LV_X: the clash is recorded by the lane that claimed `other`
+  }
   return NONE;
 }
 
-// Learned clauses watching the literals falsified by trail[base .. base+nlit).
-__device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t base, uint32_t nlit) {
+// Learned clauses watching the literals falsified in this batch: lane j <
+// nlit holds falsified literal f and its watch list pool[beg, beg + cnt).
+__device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f, uint32_t beg,
+                              uint32_t cnt) {
   __syncwarp();
   if (cd.top == 0) return;  // no learned clauses
   const long long t0 = pf_now(*w.S);
-  uint32_t f = 0, beg = 0, cnt = 0;
-  if (w.lane < nlit) {
-    f = w.trail[base + w.lane] ^ 1u;
-    const WList L = cd.wl[f];
-    beg = L.off;
-    cnt = L.len;
-  }
   uint32_t inc = cnt;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -308,7 +329,7 @@ __device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t base, uint32_t nlit)
       at = jbeg + (e - jex);
       const uint64_t ent = cd.pool[at];
       c = (uint32_t)ent;
-      pending = lit_value(w.asg, (uint32_t)(ent >> 32)) != LV_T;  // blocker
+      pending = lit_value_cd(w.asg, (uint32_t)(ent >> 32)) != LV_T;  // blocker
     }
     uint32_t g = NONE;
     uint64_t moved = 0;
@@ -319,7 +340,7 @@ __device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t base, uint32_t nlit)
         volatile uint32_t* C = cd.arena + c;
         const uint32_t other = C[CD_HDR] == jf ? C[CD_HDR + 1] : C[CD_HDR];
         bool go = true, locked = false;
-        if (lit_value(w.asg, other) == LV_F) {
+        if (lit_value_cd(w.asg, other) == LV_F) {
           locked = atomicCAS((uint32_t*)&C[1], 0u, 1u) == 0u;
           go = locked;
         }
@@ -357,10 +378,91 @@ __device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t base, uint32_t nlit)
   pf_add(*w.S, w, PF_LEARNED, t0);
 }
 
+// Static occurrence entries of one batch over the 32 lanes: lane j < nlit
+// holds falsified literal f and its occurrence list ent[beg, beg + cnt).
+__device__ __forceinline__ void static_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f,
+                                             uint32_t beg, uint32_t cnt) {
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, inc, d);
+    if (w.lane >= d) inc += y;
+  }
+  const uint32_t excl = inc - cnt;
+  const uint32_t total = __shfl_sync(FULL, inc, 31);
+  WCOUNT(w, visits, total);
+  if (nlit == 1) {  // one literal: its entries 32 at a time
+    const uint32_t f0 = __shfl_sync(FULL, f, 0), b0 = __shfl_sync(FULL, beg, 0);
+    for (uint32_t e = w.lane; e < total; e += 32) eval_entry_cd(w, cd, f0, __ldg(&w.ent[b0 + e]));
+    return;
+  }
+  if (total <= 32) {
+    // owner of entry e = the lane whose segment starts at the last start <= e
+    const bool has = cnt > 0;
+    const uint32_t starts = __reduce_or_sync(FULL, has ? (1u << excl) : 0u);
+    const uint32_t nz = __ballot_sync(FULL, has);
+    const uint32_t e = w.lane;
+    int j = 0;
+    if (e < total) j = __fns(nz, 0, __popc(starts & ((2u << e) - 1u)));
+    const uint32_t jbeg = __shfl_sync(FULL, beg, j);
+    const uint32_t jex = __shfl_sync(FULL, excl, j);
+    const uint32_t jf = __shfl_sync(FULL, f, j);
+    if (e < total) eval_entry_cd(w, cd, jf, __ldg(&w.ent[jbeg + (e - jex)]));
+    return;
+  }
+  for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+    const uint32_t e = e0 + w.lane;
+    int lo_j = 0, hi_j = 31;  // owner: smallest lane j with inc_j > e
+#pragma unroll
+    for (int s2 = 0; s2 < 5; s2++) {
+      const int mid = (lo_j + hi_j) >> 1;
+      const uint32_t v = __shfl_sync(FULL, inc, mid);
+      if (v > e) hi_j = mid; else lo_j = mid + 1;
+      if (lo_j > hi_j) lo_j = hi_j;
+    }
+    const uint32_t jbeg = __shfl_sync(FULL, beg, lo_j);
+    const uint32_t jex = __shfl_sync(FULL, excl, lo_j);
+    const uint32_t jf = __shfl_sync(FULL, f, lo_j);
+    if (e < total) eval_entry_cd(w, cd, jf, __ldg(&w.ent[jbeg + (e - jex)]));
+  }
+}
+
+// Unit propagation to a fixpoint (true on conflict), in the frontier rounds
+// of the DPLL search. Per batch of up to 32 frontier literals the lanes read
+// their literal (from the ring when it is there), clear its fresh bit, and
+// load both its occurrence-list bounds and its learned watch list before
+// the static entries and then the learned watchers are evaluated.
 __device__ bool bcp_cd(Warp& w, CdWarp& cd) {
-  return bcp_rounds(
-      w, [&](uint32_t f, uint64_t e) { eval_entry_cd(w, cd, f, e); }, [&] { cd.round++; },
-      [&](uint32_t base, uint32_t nlit) { learned_batch(w, cd, base, nlit); });
+  for (;;) {
+    __syncwarp();
+    const uint32_t hi = *(volatile uint32_t*)&w.ws->tail;
+    if (w.head >= hi) return false;
+    const uint32_t lo = w.head;
+    w.head = hi;
+    WCOUNT(w, props, hi - lo);
+    for (uint32_t base = lo; base < hi; base += 32) {
+      const uint32_t nlit = min(32u, hi - base);
+      uint32_t f = 0, beg = 0, cnt = 0, lbeg = 0, lcnt = 0;
+      if (w.lane < nlit) {
+        const uint32_t t = trail_at(w, cd, base + w.lane);
+        const uint32_t v = t >> 1;
+        atomicAnd(&w.asg[v >> 3], ~(NB_FRESH << ((v & 7u) * 4u)));  // no longer fresh
+        f = t ^ 1u;
+        beg = __ldg(&w.occ[f]);
+        cnt = __ldg(&w.occ[f + 1]) - beg;
+        if (cd.top) {
+          const WList L = cd.wl[f];
+          lbeg = L.off;
+          lcnt = L.len;
+        }
+      }
+      __syncwarp();
+      static_batch(w, cd, nlit, f, beg, cnt);
+      learned_batch(w, cd, nlit, f, lbeg, lcnt);
+      __syncwarp();
+      if (*(volatile uint32_t*)&w.ws->conflict) return true;
+    }
+  }
 }
 
 // First-UIP analysis of the recorded conflict (all lanes). Leaves the learned
@@ -495,8 +597,7 @@ __device__ void backjump_cd(Warp& w, CdWarp& cd, uint32_t lev) {
   WCOUNT(w, undone, tail - pos);
   for (uint32_t t = pos + w.lane; t < tail; t += 32) {
     const uint32_t l = w.trail[t], v = l >> 1;
-    atomicAnd(&w.asg[v >> 4], ~(3u << ((v & 15u) * 2u)));
-    cd.stamp[v] = STAMP_OPEN;
+    atomicAnd(&w.asg[v >> 3], ~(0xfu << ((v & 7u) * 4u)));
     cd.mark[v] = (l & 1u) ? 0 : MK_PHASE;
   }
   __syncwarp();
@@ -666,15 +767,49 @@ __device__ uint32_t luby_cd(uint32_t i) {
   }
 }
 
+// Highest-activity unassigned variable (ties: lowest id) over the 4-bit
+// assignment; NONE if all are assigned.
+__device__ uint32_t pick_cd(Warp& w) {
+  float best_a = -1.0f;
+  uint32_t best_v = NONE;
+  const uint32_t nwords = (w.V + 7u) >> 3;
+  for (uint32_t k = w.lane; k < nwords; k += 32) {
+    const uint32_t word = w.asg[k];
+    uint32_t un = ~(word | (word >> 1)) & 0x11111111u;  // value bits 00
+    const uint32_t lim = w.V - 8u * k;
+    if (lim < 8u) un &= (1u << (4u * lim)) - 1u;
+    while (un) {
+      const uint32_t bitpos = __ffs(un) - 1;
+      un &= un - 1u;
+      const uint32_t v = 8u * k + (bitpos >> 2);
+      const float a = w.act[v];
+      if (a > best_a || (a == best_a && v < best_v)) {
+        best_a = a;
+        best_v = v;
+      }
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    const float oa = __shfl_xor_sync(FULL, best_a, d);
+    const uint32_t ov = __shfl_xor_sync(FULL, best_v, d);
+    if (oa > best_a || (oa == best_a && ov < best_v)) {
+      best_a = oa;
+      best_v = ov;
+    }
+  }
+  return best_v;
+}
+
 // One job: an instance, or a cube of it (the job's literals as assumptions,
 // from the subtree-sharing ring), start to verdict. Returns SAT, UNSAT (for a
 // cube: no model extends it) or UNKNOWN.
 __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const TakenJob* job,
-                        int& abort_code) {
+                        uint2* ring, int& abort_code) {
   CdWarp cd;
+  cd.ring = ring;
+  for (uint32_t k = w.lane; k < RING; k += 32) ring[k] = make_uint2(NONE, NONE);
   cd.reason = S.cd_reason + slot * S.vmax;
   cd.level = S.cd_level + slot * S.vmax;
-  cd.stamp = S.cd_stamp + slot * S.vmax;
   cd.mark = S.cd_mark + slot * S.vmax;
   cd.wl = S.cd_wl + slot * 2 * S.vmax;
   cd.pool = S.cd_pool + slot * S.cd_pool_cap;
@@ -686,7 +821,6 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
   cd.pool_cap = (uint32_t)S.cd_pool_cap;
   cd.top = 0;
   cd.pool_top = 0;
-  cd.round = 1;
   cd.full = 0;
   w.inst = inst;
   w.V = (uint32_t)S.nv[inst];
@@ -698,11 +832,10 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
   w.nd = 0;
   w.nd_fixed = 0;
   w.inc = job ? job->inc : 1.0f;  // a cube starts from its donor's activities
-  const uint32_t nwords = (w.V + 15u) >> 4;
+  const uint32_t nwords = (w.V + 7u) >> 3;
   for (uint32_t k = w.lane; k < nwords; k += 32) w.asg[k] = 0u;
   for (uint32_t v = w.lane; v < w.V; v += 32) {
     if (!job) w.act[v] = 0.0f;
-    cd.stamp[v] = STAMP_OPEN;
     cd.mark[v] = 0;
   }
   clear_learnts(w, cd);
@@ -716,19 +849,19 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
   const uint32_t nu = S.nunits[inst];
   const uint32_t* un = S.units + w.c0;
   for (uint32_t k = w.lane; k < nu; k += 32)
-    if (!imply_cd(w, cd, un[k], no_reason)) record_conflict(w, un[k], NONE, NONE);
+    if (!imply_cd(w, cd, un[k], no_reason, 0u)) record_conflict(w, un[k], NONE, NONE);
   __syncwarp();
   if (w.ws->conflict) return SCUBA_UNSAT;
   if (job) {  // the cube's literals as decisions of levels 1, 2, ...
     for (int k = 0; k < job->len; k++) {
       if (bcp_cd(w, cd)) return SCUBA_UNSAT;
       const uint32_t l = job->lit[k];
-      const uint32_t val = lit_value(w.asg, l);
+      const uint32_t val = lit_value_cd(w.asg, l);
       if (val == LV_F) return SCUBA_UNSAT;
       if (val == LV_T) continue;
       if (w.lane == 0) w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
       w.nd++;
-      if (w.lane == 0) imply_cd(w, cd, l, no_reason);
+      if (w.lane == 0) imply_cd(w, cd, l, no_reason, 0u);
       __syncwarp();
     }
     w.nd_fixed = w.nd;
@@ -749,7 +882,6 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
       if (stop == 1) { abort_code = SCUBA_ERR_ABORTED; return SCUBA_UNKNOWN; }
       if (stop == 2) { abort_code = SCUBA_ERR_TIMEOUT; return SCUBA_UNKNOWN; }
       if (stop == 3) return SCUBA_UNSAT;  // the instance is SAT already; this cube is moot
-      if (cd.round > 0xfffff000u) return SCUBA_UNKNOWN;
     }
     long long t0 = pf_now(S);
     const bool confl = bcp_cd(w, cd);
@@ -793,7 +925,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
       }
       // the clause is unit once every literal but the first is false
       if (n == 1 || blev <= w.nd) {
-        if (w.lane == 0) imply_cd(w, cd, cd.learnt[0], why);
+        if (w.lane == 0) imply_cd(w, cd, cd.learnt[0], why, 0u);
         __syncwarp();
       }
       pf_add(S, w, PF_ANALYZE, t0);
@@ -820,7 +952,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
     }
     WCOUNT(w, act_reads, w.V - *(volatile uint32_t*)&w.ws->tail);
     t0 = pf_now(S);
-    const uint32_t v = pick(w);
+    const uint32_t v = pick_cd(w);
     pf_add(S, w, PF_DECIDE, t0);
     if (v == NONE) {
       // the first cube of the instance to reach a model writes it
@@ -829,8 +961,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
       won = __shfl_sync(FULL, won, 0);
       if (won && S.model)
         for (uint32_t x = w.lane; x < w.V; x += 32) {
-          const uint32_t bits = (w.asg[x >> 4] >> ((x & 15u) * 2u)) & 3u;
-          S.model[S.vb[inst] + x] = bits == 1u ? 1 : 0;
+          S.model[S.vb[inst] + x] = (nib(w.asg, x) & 3u) == NB_T ? 1 : 0;
         }
       __syncwarp();
       return SCUBA_SAT;
@@ -869,7 +1000,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
     const uint32_t lit = 2u * v + ((cd.mark[v] & MK_PHASE) ? 0u : 1u);
     if (w.lane == 0) w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
     w.nd++;
-    if (w.lane == 0) imply_cd(w, cd, lit, no_reason);
+    if (w.lane == 0) imply_cd(w, cd, lit, no_reason, 0u);
     __syncwarp();
   }
 }

@@ -407,7 +407,6 @@ struct Solve {
   // conflict-driven clause learning (per slot)
   uint64_t* cd_reason;         // [slots][vmax]
   uint32_t* cd_level;          // [slots][vmax]
-  uint32_t* cd_stamp;          // [slots][vmax]
   uint8_t* cd_mark;            // [slots][vmax]
   WList* cd_wl;                // [slots][2 vmax] learned watch lists
   uint64_t* cd_pool;           // [slots][cd_pool_cap] watch entries
@@ -545,8 +544,9 @@ __device__ __forceinline__ void eval_entry(Warp& w, uint32_t f, uint64_t e) {
 // Each round takes the trail literals assigned in the previous round (the
 // frontier) and spreads their occurrence entries over the 32 lanes:
 // visit(f, entry) evaluates one occurrence entry of the falsified literal f;
-// on_round() runs at the start of each round and after_batch(base, count)
-// after each batch of up to 32 frontier literals (all lanes, both).
+// on_round(lo, hi) runs at the start of each round (frontier trail[lo, hi))
+// and after_batch(base, count) after each batch of up to 32 frontier
+// literals (all lanes, both).
 template <class Visit, class Round, class Batch>
 __device__ __forceinline__ bool bcp_rounds(Warp& w, Visit&& visit, Round&& on_round,
                                            Batch&& after_batch) {
@@ -556,7 +556,7 @@ __device__ __forceinline__ bool bcp_rounds(Warp& w, Visit&& visit, Round&& on_ro
     if (w.head >= hi) return false;
     const uint32_t lo = w.head;
     w.head = hi;
-    on_round();
+    on_round(lo, hi);
     WCOUNT(w, props, hi - lo);
     for (uint32_t base = lo; base < hi; base += 32) {
       const uint32_t nlit = min(32u, hi - base);
@@ -628,7 +628,7 @@ __device__ __forceinline__ bool bcp_rounds(Warp& w, Visit&& visit, Round&& on_ro
 
 __device__ bool bcp(Warp& w) {
   return bcp_rounds(
-      w, [&](uint32_t f, uint64_t e) { eval_entry(w, f, e); }, [] {},
+      w, [&](uint32_t f, uint64_t e) { eval_entry(w, f, e); }, [](uint32_t, uint32_t) {},
       [](uint32_t, uint32_t) {});
 }
 
@@ -1243,6 +1243,14 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
         (S.trail_smem ? (size_t)S.vmax * wpb : 0));
     w.xtile = reinterpret_cast<__nv_bfloat16*>(tiles) + (size_t)wib * 32 * learn::NFEAT;
   }
+  uint2* ring = nullptr;
+  if (MODE == MODE_CDCL) {
+    // recent-trail ring after the per-warp assignment (and trail) areas, 16-byte aligned
+    const size_t off = ((sizeof(WarpShared) / 4) * wpb + (size_t)S.assign_words * wpb +
+                        (S.trail_smem ? (size_t)S.vmax * wpb : 0)) * 4;
+    ring = reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(smem) + ((off + 15) & ~(size_t)15)) +
+           (size_t)wib * RING;
+  }
   if (batch_failed(S.ctrl)) return;
   bool counted_idle = false;
   for (;;) {
@@ -1319,7 +1327,7 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
     } else if (moot) {
       r = SCUBA_UNSAT;  // moot: another subtree already found a model
     } else if constexpr (MODE == MODE_CDCL) {
-      r = run_cdcl(S, w, slot, inst, job, abort_code);
+      r = run_cdcl(S, w, slot, inst, job, ring, abort_code);
     } else {
       r = run_job<MODE>(S, w, inst, job, abort_code);
     }
@@ -1460,7 +1468,7 @@ struct Scratch {
   Buf occ_base, norm, occ_cnt, occ_begin, ent, units, nunits, flags;
   Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
   Buf lvlcnt, lvl_node;
-  Buf cd_reason, cd_level, cd_stamp, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
+  Buf cd_reason, cd_level, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
   int32_t last_status = 0;
@@ -1602,7 +1610,9 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   int wpb = opt->warps_per_block > 0 ? opt->warps_per_block : 8;
   int bps = opt->blocks_per_sm > 0 ? opt->blocks_per_sm : 5;
   wpb = std::min(wpb, 8);
-  const uint32_t assign_words = (uint32_t)((vmax + 15) / 16);
+  // 2 bits per variable; the clause-learning search keeps 4 (value + fresh)
+  const uint32_t assign_words = mode == dev::MODE_CDCL ? (uint32_t)((vmax + 7) / 8)
+                                                       : (uint32_t)((vmax + 15) / 16);
   const size_t smem_cap = 227 * 1024, sm_cap = 228 * 1024;
   const size_t per_warp_g = sizeof(dev::WarpShared) + (size_t)assign_words * 4;
   const size_t per_warp_s = per_warp_g + (size_t)vmax * 4;
@@ -1612,10 +1622,11 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   (void)per_warp_s;
   size_t per_warp = trail_smem ? per_warp_s : per_warp_g;
   if (mode == dev::MODE_LEARNED) per_warp += 32 * learn::NFEAT * sizeof(__nv_bfloat16);
-  size_t smem = per_warp * wpb;
+  if (mode == dev::MODE_CDCL) per_warp += dev::RING * sizeof(uint2);
+  size_t smem = per_warp * wpb + (mode == dev::MODE_CDCL ? 16 : 0);  // ring alignment
   while (wpb > 1 && smem > smem_cap) {
     wpb--;
-    smem = per_warp * wpb;
+    smem = per_warp * wpb + (mode == dev::MODE_CDCL ? 16 : 0);
   }
   if (smem > smem_cap) {
     set_error("scuba_solve_batch: instance too large for the shared-memory assignment");
@@ -1655,7 +1666,6 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
     }
     if (ensure(S.cd_reason, 8 * (size_t)slots * vmax) ||
         ensure(S.cd_level, 4 * (size_t)slots * vmax) ||
-        ensure(S.cd_stamp, 4 * (size_t)slots * vmax) ||
         ensure(S.cd_mark, (size_t)slots * vmax) ||
         ensure(S.cd_wl, 32 * (size_t)slots * vmax) ||
         ensure(S.cd_pool, 8 * (size_t)slots * arena_words) ||
@@ -1748,7 +1758,6 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.lvl_node = nullptr;
   sv.cd_reason = P<uint64_t>(S.cd_reason);
   sv.cd_level = P<uint32_t>(S.cd_level);
-  sv.cd_stamp = P<uint32_t>(S.cd_stamp);
   sv.cd_mark = P<uint8_t>(S.cd_mark);
   sv.cd_wl = P<dev::WList>(S.cd_wl);
   sv.cd_pool = P<uint64_t>(S.cd_pool);
@@ -1885,7 +1894,7 @@ extern "C" void scuba_release(void) {
   Buf* all[] = {&S.occ_base, &S.norm, &S.occ_cnt, &S.occ_begin, &S.ent, &S.units, &S.nunits,
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
                 &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node,
-                &S.cd_reason, &S.cd_level, &S.cd_stamp, &S.cd_mark, &S.cd_wl, &S.cd_pool,
+                &S.cd_reason, &S.cd_level, &S.cd_mark, &S.cd_wl, &S.cd_pool,
                 &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.h_icb, &S.h_cb, &S.h_lits,
                 &S.h_nv, &S.h_vb,
                 &S.h_verdict, &S.h_model, &S.h_stats};
