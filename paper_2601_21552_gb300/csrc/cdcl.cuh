@@ -237,19 +237,17 @@ __device__ void wl_append(Warp& w, CdWarp& cd, uint32_t g, uint64_t e) {
 // A new watch for a learned clause: the first position >= 2 whose literal is
 // not false, else the first whose literal was falsified during this round
 // (its own list brings the clause back next round), else NONE. Literals are
-// read 8 at a time (two 16-byte loads; clauses are 16-byte aligned and
-// padded).
+// read 4 at a time (16-byte loads; clauses are 16-byte aligned and padded).
 __device__ __forceinline__ uint32_t new_watch(const uint32_t* asg, const uint32_t* lits,
                                               uint32_t len) {
   const uint4* L4 = reinterpret_cast<const uint4*>(lits);
   uint32_t fresh_pos = NONE;
-  for (uint32_t q = 0; q < len; q += 8) {
+  for (uint32_t q = 0; q < len; q += 4) {
     const uint4 a = L4[q >> 2];
-    const uint4 b = q + 4 < len ? L4[(q >> 2) + 1] : make_uint4(NONE, NONE, NONE, NONE);
-    const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const uint32_t x[4] = {a.x, a.y, a.z, a.w};
     uint32_t open = 0, fr = 0;
 #pragma unroll
-    for (int i = 0; i < 8; i++) {
+    for (int i = 0; i < 4; i++) {
       if (q + i < 2 || q + i >= len) continue;
       const uint32_t n = nib(asg, x[i] >> 1);
       if (nib_value(n, x[i]) != LV_F) open |= 1u << i;
@@ -379,7 +377,8 @@ __device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f, ui
 }
 
 // Static occurrence entries of one batch over the 32 lanes: lane j < nlit
-// holds falsified literal f and its occurrence list ent[beg, beg + cnt).
+// holds falsified literal f and its occurrence list ent[beg, beg + cnt). One
+// evaluation site keeps the hot code small.
 __device__ __forceinline__ void static_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f,
                                              uint32_t beg, uint32_t cnt) {
   uint32_t inc = cnt;
@@ -391,38 +390,22 @@ __device__ __forceinline__ void static_batch(Warp& w, CdWarp& cd, uint32_t nlit,
   const uint32_t excl = inc - cnt;
   const uint32_t total = __shfl_sync(FULL, inc, 31);
   WCOUNT(w, visits, total);
-  if (nlit == 1) {  // one literal: its entries 32 at a time
-    const uint32_t f0 = __shfl_sync(FULL, f, 0), b0 = __shfl_sync(FULL, beg, 0);
-    for (uint32_t e = w.lane; e < total; e += 32) eval_entry_cd(w, cd, f0, __ldg(&w.ent[b0 + e]));
-    return;
-  }
-  if (total <= 32) {
-    // owner of entry e = the lane whose segment starts at the last start <= e
-    const bool has = cnt > 0;
-    const uint32_t starts = __reduce_or_sync(FULL, has ? (1u << excl) : 0u);
-    const uint32_t nz = __ballot_sync(FULL, has);
-    const uint32_t e = w.lane;
-    int j = 0;
-    if (e < total) j = __fns(nz, 0, __popc(starts & ((2u << e) - 1u)));
+  for (uint32_t e0 = 0; e0 < total; e0 += 32) {
+    const uint32_t e = e0 + w.lane;
+    int j = 0;  // owner: smallest lane j with inc_j > e (lane 0 alone when nlit == 1)
+    if (nlit > 1) {
+      int hi_j = 31;
+#pragma unroll
+      for (int s2 = 0; s2 < 5; s2++) {
+        const int mid = (j + hi_j) >> 1;
+        const uint32_t v = __shfl_sync(FULL, inc, mid);
+        if (v > e) hi_j = mid; else j = mid + 1;
+        if (j > hi_j) j = hi_j;
+      }
+    }
     const uint32_t jbeg = __shfl_sync(FULL, beg, j);
     const uint32_t jex = __shfl_sync(FULL, excl, j);
     const uint32_t jf = __shfl_sync(FULL, f, j);
-    if (e < total) eval_entry_cd(w, cd, jf, __ldg(&w.ent[jbeg + (e - jex)]));
-    return;
-  }
-  for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-    const uint32_t e = e0 + w.lane;
-    int lo_j = 0, hi_j = 31;  // owner: smallest lane j with inc_j > e
-#pragma unroll
-    for (int s2 = 0; s2 < 5; s2++) {
-      const int mid = (lo_j + hi_j) >> 1;
-      const uint32_t v = __shfl_sync(FULL, inc, mid);
-      if (v > e) hi_j = mid; else lo_j = mid + 1;
-      if (lo_j > hi_j) lo_j = hi_j;
-    }
-    const uint32_t jbeg = __shfl_sync(FULL, beg, lo_j);
-    const uint32_t jex = __shfl_sync(FULL, excl, lo_j);
-    const uint32_t jf = __shfl_sync(FULL, f, lo_j);
     if (e < total) eval_entry_cd(w, cd, jf, __ldg(&w.ent[jbeg + (e - jex)]));
   }
 }
