@@ -63,6 +63,9 @@ constexpr uint32_t CD_HDR = 4;
 constexpr uint64_t WATCH_GONE = ~0ull;     // tombstone of a moved watch entry
 constexpr uint32_t NB_T = 1u, NB_F = 2u, NB_FRESH = 4u;  // assignment nibble bits
 constexpr uint32_t RING = 128;  // recent-trail entries per warp in shared memory
+constexpr uint32_t CAND = 96;   // current-level literals awaiting resolution, per warp
+// shared memory per warp for the clause-learning search (16-byte multiple)
+constexpr uint32_t CD_SMEM_WARP = RING * 8 + CAND * 8;
 constexpr uint8_t MK_PHASE = 1, MK_SEEN = 2;
 
 // Profile counters (only when the caller passed a profile array): lane 0
@@ -95,7 +98,9 @@ struct CdWarp {
   uint32_t* arena;    // [arena_words]
   uint32_t* cl_off;   // [arena_words / 8] arena offset of each learned clause, oldest first
   uint32_t* learnt;   // [V] clause under construction
+  uint32_t* pos;      // [V] trail position of each assigned variable
   uint2* ring;        // [RING] shared memory: {literal, trail position} of recent claims
+  uint2* cand;        // [CAND] shared memory: analysis queue {trail position, literal}
   uint32_t arena_words, pool_cap;
   uint32_t top;       // first free arena word
   uint32_t ncl;       // learned clauses in the arena
@@ -137,6 +142,7 @@ __device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64
   const uint32_t pos = atomicAdd(&w.ws->tail, 1u);
   w.trail[pos] = l;
   cd.ring[pos & (RING - 1u)] = make_uint2(l, pos);
+  cd.pos[v] = pos;
   cd.reason[v] = why;
   cd.level[v] = w.nd;
   return true;
@@ -169,16 +175,13 @@ __device__ void eval_long_cd(Warp& w, CdWarp& cd, uint32_t local) {
       fresh_false = true;
     }
   }
-  if (n_open == 0) {
-    record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
-    return;
-  }
-  if (fresh_false) return;  // a literal falsified this round: next round
-  if (!imply_cd(w, cd, open_lit, (uint64_t)(LONG_CLAUSE | local)))
+  if (n_open == 1 && fresh_false) return;  // a literal falsified this round: next round
+  if (n_open == 0 || !imply_cd(w, cd, open_lit, (uint64_t)(LONG_CLAUSE | local)))
     record_conflict(w, LONG_CLAUSE | local, NONE, NONE);
 }
 
-// One occurrence entry of the falsified (old) literal f.
+// One occurrence entry of the falsified (old) literal f: (f | a) with b ==
+// NONE, (f | a | b), or a long clause. One claim site and one conflict site.
 __device__ __forceinline__ void eval_entry_cd(Warp& w, CdWarp& cd, uint32_t f, uint64_t e) {
   const uint32_t a = (uint32_t)e, b = (uint32_t)(e >> 32);
   if (a & LONG_CLAUSE) {
@@ -187,24 +190,27 @@ __device__ __forceinline__ void eval_entry_cd(Warp& w, CdWarp& cd, uint32_t f, u
   }
   const uint32_t na = nib(w.asg, a >> 1);
   const uint32_t va = nib_value(na, a);
-  if (b == NONE) {  // binary (f | a): a's reason is {f}
-    if (va == LV_T) return;
-    if (va == LV_F || !imply_cd(w, cd, a, (uint64_t)f | ((uint64_t)NONE << 32)))
-      record_conflict(w, f, a, NONE);
-    return;
+  uint32_t nb = 0, vb = LV_F;  // a binary entry has no third literal: read it as false
+  if (b != NONE) {
+    nb = nib(w.asg, b >> 1);
+    vb = nib_value(nb, b);
   }
-  const uint32_t nb = nib(w.asg, b >> 1);
-  const uint32_t vb = nib_value(nb, b);  // ternary (f | a | b)
   if (va == LV_T || vb == LV_T) return;
-  if (va == LV_F && vb == LV_F) {
-    record_conflict(w, f, a, b);
-  } else if (va == LV_F) {
-    if (na & NB_FRESH) return;  // next round
-    if (!imply_cd(w, cd, b, (uint64_t)f | ((uint64_t)a << 32))) record_conflict(w, f, a, b);
-  } else if (vb == LV_F) {
-    if (nb & NB_FRESH) return;
-    if (!imply_cd(w, cd, a, (uint64_t)f | ((uint64_t)b << 32))) record_conflict(w, f, a, b);
+  uint32_t unit = NONE, other = NONE;  // the literal to imply, the false one beside f
+  if (va == LV_U && vb == LV_F) {
+    if (nb & NB_FRESH) return;  // b falsified this round: next round
+    unit = a;
+    other = b;
+  } else if (vb == LV_U && va == LV_F) {
+    if (na & NB_FRESH) return;
+    unit = b;
+    other = a;
+  } else if (va == LV_U || vb == LV_U) {
+    return;  // two open literals
   }
+  if (unit == NONE ||
+      !imply_cd(w, cd, unit, (uint64_t)f | ((uint64_t)other << 32)))
+    record_conflict(w, f, a, b);
 }
 
 // Append entry e to literal g's watch list (all lanes, uniform arguments).
@@ -458,6 +464,11 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
   uint32_t n = 1, path = 0, p = NONE;
   uint32_t r0 = w.ws->cl[0], r1 = w.ws->cl[1], r2 = w.ws->cl[2];
   int64_t idx = (int64_t)*(volatile uint32_t*)&w.ws->tail - 1;
+  // Current-level literals not yet resolved wait in cd.cand with their trail
+  // positions; the newest is the next to resolve. If more than CAND wait at
+  // once, the rest of this analysis scans the trail for seen marks instead.
+  uint32_t ncand = 0;
+  bool overflow = false;
   bool big = false;
   for (;;) {
     // the literals of the clause: static entry (up to three codes), a long
@@ -480,46 +491,81 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
       uint32_t q = NONE;
       if (k < cnt) q = src ? src[k] : csr ? code_of(csr[k]) : (k == 0 ? r0 : k == 1 ? r1 : r2);
       const uint32_t v = q >> 1;
-      bool take = q != NONE && (p == NONE || v != (p >> 1));
-      if (take) take = !(cd.mark[v] & MK_SEEN);
-      uint32_t lv = 0;
-      if (take) {
+      bool take = false;
+      uint32_t mk = 0, lv = 0, ps = 0;
+      if (q != NONE && (p == NONE || v != (p >> 1))) {
+        mk = cd.mark[v];  // three independent loads
         lv = cd.level[v];
-        take = lv > 0;
+        ps = cd.pos[v];
+        take = !(mk & MK_SEEN) && lv > 0;
       }
       // one lane per variable (a long clause may repeat a literal)
       const uint32_t grp = __match_any_sync(FULL, take ? v : NONE);
       if (take && __ffs(grp) - 1 != w.lane) take = false;
       if (take) {
-        cd.mark[v] |= MK_SEEN;
+        cd.mark[v] = mk | MK_SEEN;
         const float a = w.act[v] + w.inc;
         w.act[v] = a;
         big |= a > 1e20f;
       }
-      path += __popc(__ballot_sync(FULL, take && lv >= lvl));
+      const bool cur = take && lv >= lvl;
+      const uint32_t curm = __ballot_sync(FULL, cur);
+      path += __popc(curm);
+      if (!overflow) {
+        if (ncand + __popc(curm) <= CAND) {
+          if (cur) cd.cand[ncand + __popc(curm & ((1u << w.lane) - 1u))] = make_uint2(ps, q ^ 1u);
+          ncand += __popc(curm);
+        } else {
+          overflow = true;
+        }
+      }
       const uint32_t lowm = __ballot_sync(FULL, take && lv < lvl);
       if (take && lv < lvl) cd.learnt[n + __popc(lowm & ((1u << w.lane) - 1u))] = q;
       n += __popc(lowm);
       __syncwarp();
     }
-    // the newest seen literal on the trail is the next to resolve; a
-    // conflict without a current-level literal, or a scan that runs off the
+    // a conflict without a current-level literal, or a scan that runs off the
     // trail, means the search state is inconsistent: give up (n = 0)
     if (path == 0) return 0;
-    for (;;) {
-      if (idx < 0) return 0;
-      const int64_t pos = idx - w.lane;
-      bool s = false;
-      if (pos >= 0) s = (cd.mark[w.trail[pos] >> 1] & MK_SEEN) != 0;
-      const uint32_t m = __ballot_sync(FULL, s);
-      if (m) {
-        idx -= __ffs(m) - 1;
-        break;
+    if (!overflow) {
+      // the newest waiting literal (trail positions are distinct)
+      uint32_t key = 0, kk = 0;  // key = position + 1
+      for (uint32_t k = w.lane; k < ncand; k += 32) {
+        const uint32_t x = cd.cand[k].x + 1u;
+        if (x > key) {
+          key = x;
+          kk = k;
+        }
       }
-      idx -= 32;
+      for (int d = 16; d > 0; d >>= 1) {
+        const uint32_t ok = __shfl_xor_sync(FULL, key, d), oi = __shfl_xor_sync(FULL, kk, d);
+        if (ok > key) {
+          key = ok;
+          kk = oi;
+        }
+      }
+      if (key == 0) return 0;
+      p = cd.cand[kk].y;
+      idx = (int64_t)key - 2;  // where a trail scan would continue
+      __syncwarp();
+      if (w.lane == 0) cd.cand[kk] = cd.cand[ncand - 1];
+      ncand--;
+    } else {
+      for (;;) {  // the newest seen literal on the trail
+        if (idx < 0) return 0;
+        const int64_t pos = idx - w.lane;
+        bool sn = false;
+        if (pos >= 0) sn = (cd.mark[w.trail[pos] >> 1] & MK_SEEN) != 0;
+        const uint32_t m = __ballot_sync(FULL, sn);
+        if (m) {
+          idx -= __ffs(m) - 1;
+          break;
+        }
+        idx -= 32;
+      }
+      p = w.trail[idx];
+      idx--;
     }
-    p = w.trail[idx];
-    idx--;
     __syncwarp();
     if (w.lane == 0) cd.mark[p >> 1] &= (uint8_t)~MK_SEEN;
     __syncwarp();
@@ -790,6 +836,8 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
                         uint2* ring, int& abort_code) {
   CdWarp cd;
   cd.ring = ring;
+  cd.cand = ring + RING;
+  cd.pos = S.cd_pos + slot * S.vmax;
   for (uint32_t k = w.lane; k < RING; k += 32) ring[k] = make_uint2(NONE, NONE);
   cd.reason = S.cd_reason + slot * S.vmax;
   cd.level = S.cd_level + slot * S.vmax;

@@ -406,6 +406,7 @@ struct Solve {
   int64_t* lvl_node;           // [slots][MAX_TRACE_DEPTH] node of each open level
   // conflict-driven clause learning (per slot)
   uint64_t* cd_reason;         // [slots][vmax]
+  uint32_t* cd_pos;            // [slots][vmax]
   uint32_t* cd_level;          // [slots][vmax]
   uint8_t* cd_mark;            // [slots][vmax]
   WList* cd_wl;                // [slots][2 vmax] learned watch lists
@@ -1245,11 +1246,12 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
   }
   uint2* ring = nullptr;
   if (MODE == MODE_CDCL) {
-    // recent-trail ring after the per-warp assignment (and trail) areas, 16-byte aligned
+    // recent-trail ring and analysis queue after the per-warp assignment (and
+    // trail) areas, 16-byte aligned
     const size_t off = ((sizeof(WarpShared) / 4) * wpb + (size_t)S.assign_words * wpb +
                         (S.trail_smem ? (size_t)S.vmax * wpb : 0)) * 4;
-    ring = reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(smem) + ((off + 15) & ~(size_t)15)) +
-           (size_t)wib * RING;
+    ring = reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(smem) +
+                                    ((off + 15) & ~(size_t)15) + (size_t)wib * CD_SMEM_WARP);
   }
   if (batch_failed(S.ctrl)) return;
   bool counted_idle = false;
@@ -1468,7 +1470,7 @@ struct Scratch {
   Buf occ_base, norm, occ_cnt, occ_begin, ent, units, nunits, flags;
   Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
   Buf lvlcnt, lvl_node;
-  Buf cd_reason, cd_level, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
+  Buf cd_reason, cd_pos, cd_level, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
   int32_t last_status = 0;
@@ -1622,7 +1624,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   (void)per_warp_s;
   size_t per_warp = trail_smem ? per_warp_s : per_warp_g;
   if (mode == dev::MODE_LEARNED) per_warp += 32 * learn::NFEAT * sizeof(__nv_bfloat16);
-  if (mode == dev::MODE_CDCL) per_warp += dev::RING * sizeof(uint2);
+  if (mode == dev::MODE_CDCL) per_warp += dev::CD_SMEM_WARP;
   size_t smem = per_warp * wpb + (mode == dev::MODE_CDCL ? 16 : 0);  // ring alignment
   while (wpb > 1 && smem > smem_cap) {
     wpb--;
@@ -1665,6 +1667,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
       return SCUBA_ERR_ARG;
     }
     if (ensure(S.cd_reason, 8 * (size_t)slots * vmax) ||
+        ensure(S.cd_pos, 4 * (size_t)slots * vmax) ||
         ensure(S.cd_level, 4 * (size_t)slots * vmax) ||
         ensure(S.cd_mark, (size_t)slots * vmax) ||
         ensure(S.cd_wl, 32 * (size_t)slots * vmax) ||
@@ -1757,6 +1760,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.lvlcnt = nullptr;
   sv.lvl_node = nullptr;
   sv.cd_reason = P<uint64_t>(S.cd_reason);
+  sv.cd_pos = P<uint32_t>(S.cd_pos);
   sv.cd_level = P<uint32_t>(S.cd_level);
   sv.cd_mark = P<uint8_t>(S.cd_mark);
   sv.cd_wl = P<dev::WList>(S.cd_wl);
@@ -1894,7 +1898,7 @@ extern "C" void scuba_release(void) {
   Buf* all[] = {&S.occ_base, &S.norm, &S.occ_cnt, &S.occ_begin, &S.ent, &S.units, &S.nunits,
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
                 &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node,
-                &S.cd_reason, &S.cd_level, &S.cd_mark, &S.cd_wl, &S.cd_pool,
+                &S.cd_reason, &S.cd_pos, &S.cd_level, &S.cd_mark, &S.cd_wl, &S.cd_pool,
                 &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.h_icb, &S.h_cb, &S.h_lits,
                 &S.h_nv, &S.h_vb,
                 &S.h_verdict, &S.h_model, &S.h_stats};
