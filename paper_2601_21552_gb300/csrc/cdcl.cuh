@@ -676,6 +676,8 @@ __device__ void clear_learnts(Warp& w, CdWarp& cd) {
   __syncwarp();
 }
 
+__device__ bool rebuild_watches(Warp& w, CdWarp& cd);
+
 // Learned-clause database maintenance at the bottom level (no reason above it
 // refers to a learned clause). With drop_half, keep the newer half of the
 // clauses and every clause whose LBD is at most 3 (the "glue" clauses that
@@ -727,7 +729,14 @@ __device__ bool reduce_db(Warp& w, CdWarp& cd, bool drop_half) {
   }
   cd.top = run_words;
   cd.ncl = run_cl;
-  // watch lists: count, exclusive scan of capacities, fill
+  return rebuild_watches(w, cd);
+}
+
+// Every watch list built afresh from the learned clauses' first two literals
+// (count, exclusive scan of capacities, fill); this also compacts the pool.
+// Returns false when the lists would take more than half of the pool.
+__device__ bool rebuild_watches(Warp& w, CdWarp& cd) {
+  const uint32_t run_cl = cd.ncl;
   const uint32_t nl = 2u * w.V;
   for (uint32_t k = w.lane; k < nl; k += 32) cd.wl[k] = WList{0u, 0u, 0u, 0u};
   __syncwarp();
@@ -794,6 +803,102 @@ __device__ uint32_t luby_cd(uint32_t i) {
     if (i == (1u << k) - 1u || k == 31) return 1u << (k - 1);
     i -= (1u << (k - 1)) - 1u;
   }
+}
+
+// Learned clauses handed to a cube with its assumptions (all lanes): the
+// newest clauses of at most 12 literals and LBD at most 4, as many as fit
+// dst[JOB_CLS_WORDS] = [count, words used, offsets[JOB_CLS_MAX], records
+// {len, lbd, literals}]. Every learned clause is implied by the formula, so
+// the cube may use them whatever its assumptions.
+__device__ void export_clauses(Warp& w, CdWarp& cd, uint32_t* dst) {
+  constexpr uint32_t base = 2 + JOB_CLS_MAX;
+  uint32_t m = 0, used = base;
+  for (int64_t k0 = (int64_t)cd.ncl - 1; k0 >= 0 && m < JOB_CLS_MAX; k0 -= 32) {
+    const int64_t k = k0 - w.lane;
+    uint32_t off = 0, len = 0, lbd = 0, words = 0;
+    if (k >= 0) {
+      off = cd.cl_off[k];
+      len = cd.arena[off];
+      lbd = cd.arena[off + 2];
+      if (len <= 12u && lbd <= 4u) words = len + 2u;
+    }
+    uint32_t inc = words;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, d);
+      if (w.lane >= d) inc += y;
+    }
+    const bool ok = words > 0 && used + inc <= JOB_CLS_WORDS;
+    const uint32_t okm = __ballot_sync(FULL, ok);
+    const uint32_t rank = __popc(okm & ((1u << w.lane) - 1u));
+    if (ok && m + rank < JOB_CLS_MAX) {
+      const uint32_t at = used + inc - words;
+      dst[2 + m + rank] = at;
+      dst[at] = len;
+      dst[at + 1] = lbd;
+      for (uint32_t q = 0; q < len; q++) dst[at + 2 + q] = cd.arena[off + CD_HDR + q];
+    }
+    const uint32_t taken = min((uint32_t)__popc(okm), JOB_CLS_MAX - m);
+    // the prefix sums grow with the lane, so the clauses that fit are a prefix
+    const int last = taken ? __fns(okm, 0, taken) : -1;
+    if (taken) used += __shfl_sync(FULL, inc, last);
+    m += taken;
+    if (__popc(okm) < __popc(__ballot_sync(FULL, words > 0))) break;  // buffer full
+  }
+  if (w.lane == 0) {
+    dst[0] = m;
+    dst[1] = used;
+  }
+  __syncwarp();
+}
+
+// The clauses a donor attached to this cube (see export_clauses) into the
+// empty database, then its watch lists. Returns false (the database is left
+// empty) if they do not fit.
+__device__ bool import_clauses(Warp& w, CdWarp& cd, const uint32_t* src) {
+  const uint32_t m = min(src[0], JOB_CLS_MAX);
+  uint32_t top = 0;
+  for (uint32_t k0 = 0; k0 < m; k0 += 32) {
+    const uint32_t k = k0 + w.lane;
+    uint32_t at = 0, len = 0, words = 0;
+    if (k < m) {
+      at = src[2 + k];
+      if (at >= 2 + JOB_CLS_MAX && at + 2 < JOB_CLS_WORDS) {
+        len = src[at];
+        if (at + 2 + len <= JOB_CLS_WORDS && len >= 2u && len <= 12u) words = clause_words(len);
+      }
+    }
+    uint32_t inc = words;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, inc, d);
+      if (w.lane >= d) inc += y;
+    }
+    const uint32_t c = top + inc - words;
+    const uint32_t okm = __ballot_sync(FULL, words > 0);
+    if (!__all_sync(FULL, !words || c + words <= cd.arena_words)) {  // no room
+      clear_learnts(w, cd);
+      return false;
+    }
+    if (words) {
+      cd.arena[c] = len;
+      cd.arena[c + 1] = 0u;
+      cd.arena[c + 2] = src[at + 1];
+      cd.arena[c + 3] = 0u;
+      for (uint32_t q = 0; q < words - CD_HDR; q++)
+        cd.arena[c + CD_HDR + q] = q < len ? src[at + 2 + q] : NONE;
+      cd.cl_off[cd.ncl + __popc(okm & ((1u << w.lane) - 1u))] = c;
+    }
+    top += __shfl_sync(FULL, inc, 31);
+    cd.ncl += __popc(okm);
+    __syncwarp();
+  }
+  cd.top = top;
+  if (!rebuild_watches(w, cd)) {
+    clear_learnts(w, cd);
+    return false;
+  }
+  return true;
 }
 
 // Highest-activity unassigned variable (ties: lowest id) over the 4-bit
@@ -870,6 +975,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
     cd.mark[v] = 0;
   }
   clear_learnts(w, cd);
+  if (job && job->cls) import_clauses(w, cd, job->cls);  // the donor's clauses
   if (w.lane == 0) {
     w.ws->tail = 0;
     w.ws->conflict = 0;
@@ -1009,7 +1115,9 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
         const uint32_t k = w.nd_fixed;
         if (w.lane == 0) atomicAdd(&S.pending[inst], 1u);
         __syncwarp();
-        if (ring_push(S, w, inst, k + 1, w.trail, w.dstack, k)) {
+        if (ring_push(S, w, inst, k + 1, w.trail, w.dstack, k, [&](uint32_t cell) {
+              export_clauses(w, cd, S.job_cls + (size_t)cell * JOB_CLS_WORDS);
+            })) {
           w.nd_fixed = k + 1;
           if (w.lane == 0) {
             atomicAdd(&S.ctrl->jobs_split, 1u);

@@ -46,6 +46,9 @@ constexpr uint32_t UNIT_BIT = 0x40000000u;
 constexpr uint32_t FLIP = 0x80000000u;
 constexpr uint32_t F_EMPTY = 1u, F_BAD = 2u;
 constexpr int MAX_PREFIX = 248;   // literals in a split job's prefix
+// Learned clauses a clause-learning donor attaches to a cube: [count, words
+// used, offset of each clause (JOB_CLS_MAX), records {len, lbd, literals}].
+constexpr uint32_t JOB_CLS_MAX = 256, JOB_CLS_WORDS = 4096;
 
 __device__ __forceinline__ uint32_t code_of(int32_t l) {
   int32_t v = l > 0 ? l : -l;
@@ -415,6 +418,8 @@ struct Solve {
   uint32_t* cd_arena;          // [slots][cd_arena_words]
   uint32_t* cd_clidx;          // [slots][cd_arena_words / 8] clause offsets
   int64_t cd_arena_words, cd_pool_cap;
+  uint32_t* job_cls;           // [ring_cap][JOB_CLS_WORDS] clauses shared with a cube
+  uint32_t* cls_copy;          // [slots][JOB_CLS_WORDS] a taken cube's clauses
   int restart_unit;            // conflicts per Luby unit
 };
 
@@ -920,9 +925,12 @@ __device__ __forceinline__ void set_status(const Solve& S, int32_t st) {
 
 // ---- job ring (bounded MPMC queue, Vyukov) --------------------------------
 
+// extra(cell) runs (all lanes) after the cell is filled and before it is
+// published: the clause-learning search attaches learned clauses there.
+template <class Extra>
 __device__ bool ring_push(const Solve& S, const Warp& w, int inst, uint32_t plen,
                           const uint32_t* prefix_src_trail, const uint32_t* dpos,
-                          uint32_t flip_index) {
+                          uint32_t flip_index, Extra&& extra) {
   // called by all lanes; lane 0 reserves
   Ctrl* C = S.ctrl;
   uint32_t slot = NONE;
@@ -957,11 +965,18 @@ __device__ bool ring_push(const Solve& S, const Warp& w, int inst, uint32_t plen
     cell->len = (int32_t)plen;
     cell->inc = w.inc;
   }
+  extra(slot & (S.ring_cap - 1));
   __threadfence();
   __syncwarp();
   if (w.lane == 0) atomicExch(&cell->seq, slot + 1);
   __syncwarp();
   return true;
+}
+
+__device__ bool ring_push(const Solve& S, const Warp& w, int inst, uint32_t plen,
+                          const uint32_t* prefix_src_trail, const uint32_t* dpos,
+                          uint32_t flip_index) {
+  return ring_push(S, w, inst, plen, prefix_src_trail, dpos, flip_index, [](uint32_t) {});
 }
 
 // Try to take a job; returns slot or NONE.
@@ -1038,6 +1053,7 @@ struct TakenJob {
   const uint32_t* lit;  // assumptions, in order
   int32_t len;
   float inc;            // activities were copied into the warp's act[] already
+  const uint32_t* cls;  // clause learning: the donor's clauses (slot copy), or NULL
 };
 
 template <int MODE>
@@ -1274,6 +1290,14 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
       taken.lit = pre;
       taken.len = len;
       taken.inc = cell->inc;
+      taken.cls = nullptr;
+      if (MODE == MODE_CDCL) {  // the donor's learned clauses, copied out too
+        const uint32_t* src = S.job_cls + (size_t)(slot_j & (S.ring_cap - 1)) * JOB_CLS_WORDS;
+        uint32_t* dst = S.cls_copy + slot * JOB_CLS_WORDS;
+        const uint32_t words = min(src[1], JOB_CLS_WORDS);
+        for (uint32_t k = lane; k < words; k += 32) dst[k] = src[k];
+        taken.cls = dst;
+      }
       __syncwarp();
       ring_release(S, slot_j, lane);
       job = &taken;
@@ -1471,6 +1495,7 @@ struct Scratch {
   Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
   Buf lvlcnt, lvl_node;
   Buf cd_reason, cd_pos, cd_level, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
+  Buf job_cls, cls_copy;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
   int32_t last_status = 0;
@@ -1674,7 +1699,9 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
         ensure(S.cd_pool, 8 * (size_t)slots * arena_words) ||
         ensure(S.cd_learnt, 4 * (size_t)slots * vmax) ||
         ensure(S.cd_arena, 4 * (size_t)slots * arena_words) ||
-        ensure(S.cd_clidx, 4 * (size_t)slots * (arena_words / 8))) {
+        ensure(S.cd_clidx, 4 * (size_t)slots * (arena_words / 8)) ||
+        ensure(S.job_cls, 4 * (size_t)ring_cap * dev::JOB_CLS_WORDS) ||
+        ensure(S.cls_copy, 4 * (size_t)slots * dev::JOB_CLS_WORDS)) {
       set_error("scuba_solve_batch: out of device memory for clause-learning scratch");
       return SCUBA_ERR_NOMEM;
     }
@@ -1769,6 +1796,8 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.cd_learnt = P<uint32_t>(S.cd_learnt);
   sv.cd_arena = P<uint32_t>(S.cd_arena);
   sv.cd_clidx = P<uint32_t>(S.cd_clidx);
+  sv.job_cls = P<uint32_t>(S.job_cls);
+  sv.cls_copy = P<uint32_t>(S.cls_copy);
   sv.cd_arena_words = arena_words;
   sv.restart_unit = opt->restart_unit > 0 ? opt->restart_unit : 100;
   std::memset(&sv.tr, 0, sizeof(sv.tr));
@@ -1899,7 +1928,8 @@ extern "C" void scuba_release(void) {
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
                 &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node,
                 &S.cd_reason, &S.cd_pos, &S.cd_level, &S.cd_mark, &S.cd_wl, &S.cd_pool,
-                &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.h_icb, &S.h_cb, &S.h_lits,
+                &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.job_cls, &S.cls_copy, &S.h_icb,
+                &S.h_cb, &S.h_lits,
                 &S.h_nv, &S.h_vb,
                 &S.h_verdict, &S.h_model, &S.h_stats};
   for (Buf* x : all) {
