@@ -41,19 +41,19 @@ METRIC = "verdicts/sec + BCP propagations/sec on 1 GB300, learned vs plain, bit-
 WORKLOAD = "partition queries, 16-bit inputs (4,096 per GPU)"
 
 
-# DRAM traffic of the plain search kernel from one ncu capture (the 1,024-query
-# case of profiles/k_solve_partition16_1024.md: 0.744 GB for 1.05e9
-# propagations), per propagation, valid only for the kernel sources it was
-# taken on (sha256 prefix of solver.cu + learn.cuh); scaled to a full launch
-# by the propagations it processes.
-PROFILED_SOURCES = "dcbcae6f9b12e8c3"
-DRAM_BYTES_PER_PROPAGATION = {"plain": 0.744e9 / (3.9957e9 * 0.2626)}
+# DRAM traffic of the clause-learning search kernel from one single-pass ncu
+# capture of a full launch (profiles/k_solve_cdcl_partition16.md: 6.69 GB read +
+# 5.27 GB written for 1.480e8 propagations), per propagation, valid only for
+# the kernel sources it was taken on (sha256 prefix of solver.cu + learn.cuh +
+# cdcl.cuh); scaled to each launch by the propagations it processes.
+PROFILED_SOURCES = "06fb903fc3309244"
+DRAM_BYTES_PER_PROPAGATION = {"cdcl": (6.69e9 + 5.27e9) / 1.4798e8}
 
 
 def _kernel_sources_sha() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("solver.cu", "learn.cuh"):
+    for f in ("solver.cu", "learn.cuh", "cdcl.cuh"):
         with open(os.path.join(ROOT, "paper_2601_21552_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -424,6 +424,8 @@ def run_ours(args):
                                  and _kernel_sources_sha() == PROFILED_SOURCES else None),
                      "traffic_unit": "bytes per launch (ncu, scaled by propagations)",
                      "kernel": f"k_solve ({arms[0]} search)", "peak_source": src,
+                     "limiter": "latency: dependent L1/L2 loads and instruction issue "
+                                "per propagation round, DRAM mostly idle",
                      "search_ms": head["search_ms"]},
         "clocks": clk.summary(),
     }
