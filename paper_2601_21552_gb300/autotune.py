@@ -33,9 +33,9 @@ SPACE = {
 # clause learning: decisions before a job may give away cubes, decisions
 # between checks for idle warps, conflicts per Luby restart unit
 SPACE_CDCL = {
-    "split_min": [64, 256, 1024],
-    "split_interval": [4, 16, 64],
-    "restart_unit": [50, 100, 200],
+    "split_min": [4, 8, 16, 32],
+    "split_interval": [8, 16, 32],
+    "restart_unit": [12, 25, 40],
 }
 
 
