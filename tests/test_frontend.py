@@ -1,0 +1,171 @@
+"""Front end (program description -> per-access queries, UAF pass), on the
+CPU with the oracle as the solver. Pins: the paper's worked examples written
+as programs (tests/golden/programs, each access's expected verdict cited),
+the closed forms of the bounds and partition families written as programs,
+exact subtraction semantics, the use-after-free rule of Sec. V-C, and
+malformed programs."""
+import glob
+import os
+
+import pytest
+
+import oracle
+from closed_forms import bounds_algebra, partition_algebra
+from ir_eval import evaluate
+from paper_2601_21552_gb300 import frontend as F
+from workloads import queries
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PROGRAMS = sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "programs", "*.kp")))
+
+
+def _solve(accs):
+    r = oracle.solve_queries([a.ir for a in accs], max_words=16)
+    return [int(v) for v in r["verdict"]], r["words"]
+
+
+@pytest.mark.parametrize("path", PROGRAMS, ids=os.path.basename)
+def test_worked_examples_as_programs(path):
+    prog = F.parse(open(path).read())
+    assert "cite" in prog.meta
+    accs = F.queries(prog)
+    assert accs and all(a.meta.get("expect") in ("SAT", "UNSAT") for a in accs)
+    got, words = _solve(accs)
+    assert got == [1 if a.meta["expect"] == "SAT" else 0 for a in accs]
+    for a, v, wd in zip(accs, got, words):  # every witness satisfies its query
+        if v == 1:
+            assert evaluate(a.ir, [int(x) for x in wd[:len(a.inputs)]])
+    want_uaf = prog.meta.get("uaf", "")
+    want = sorted(tuple(x.strip().split(":")) for x in want_uaf.split(";") if x.strip())
+    assert sorted((u.what, u.name) for u in F.use_after_free(prog)) == want
+
+
+def bounds_program(w, k1, k0, a, c, guard):
+    """The config-1 template as a program: one global allocation of k1*n + k0
+    elements, blocks of bdim threads, an unknown number of blocks."""
+    body = f"access b[{a} * idx + {c}]"
+    if guard:
+        body = f"if idx < m\n    {body}\n  end"
+    return f"""input n {w}
+input bdim {w}
+malloc buf {k1} * n + {k0}
+launch k grid(?) block(bdim) args(buf, n)
+kernel k(b, m)
+  let idx = blockIdx.x * blockDim.x + threadIdx.x
+  {body}
+end
+"""
+
+
+def partition_program(w, k1, k0, a, c, k, j, guard):
+    """The config-2 template as a program: the allocation split at i*(n/k)
+    (the base is partition 0), the access into partition j."""
+    parts = "\n".join(f"  partition p{i} = b + {i} * (m)" for i in range(1, k))
+    ptr = "b" if j == 0 else f"p{j}"
+    body = f"access {ptr}[{a} * idx + {c}]"
+    if guard:
+        body = f"if idx < m\n    {body}\n  end"
+    return f"""input n {w}
+input bdim {w}
+malloc buf {k1} * n + {k0}
+launch k grid(?) block(bdim) args(buf, n)
+kernel k(b, nn)
+  let m = nn / {k}
+{parts}
+  let idx = blockIdx.x * blockDim.x + threadIdx.x
+  {body}
+end
+"""
+
+
+@pytest.mark.parametrize("w", [6, 8])
+def test_families_as_programs_match_closed_forms(w):
+    bp = [queries.config1_params(8100 + i, w=w) for i in range(40)]
+    pp = [queries.config2_params(8200 + i, w=w) for i in range(40)]
+    accs = []
+    for p in bp:
+        accs += F.queries(F.parse(bounds_program(**p)), bid_width=w)
+    for p in pp:
+        accs += F.queries(F.parse(partition_program(**p)), bid_width=w)
+    got, _ = _solve(accs)
+    want = [int(bounds_algebra(**p)) for p in bp] + [int(partition_algebra(**p)) for p in pp]
+    assert got == want
+    assert set(want) == {0, 1}
+
+
+def test_program_query_equals_template_query():
+    """Same verdicts as the hand-built templates on shared seeds (the
+    templates are pinned by brute force at w <= 6)."""
+    ps = [queries.config1_params(8300 + i, w=5) for i in range(24)]
+    accs = [F.queries(F.parse(bounds_program(**p)), bid_width=5)[0] for p in ps]
+    got, _ = _solve(accs)
+    for p, g in zip(ps, got):
+        bf, _ = oracle.brute_force(queries.bounds_query(**p).to_array(), max_bits=24)
+        assert g == bf
+
+
+def test_exact_subtraction():
+    """Partition sizes and offsets are exact integers: a partition whose next
+    one starts before it has a negative size, and an offset below the base is
+    out of bounds, without wrap-around (b's own accesses would be checked
+    against its first partition, [0, x), so the offset checks use f)."""
+    text = """input n 6
+input d 6
+malloc buf 64
+malloc flat 64
+launch k grid(1) block(1) args(buf, flat, n, d)
+kernel k(b, f, x, y)
+  partition p1 = b + x
+  partition p2 = b + y
+  access p1[0]       @expect SAT
+  access f[x - y]    @expect SAT
+  if x < y
+    access f[y - x - 1]   @expect UNSAT
+  end
+end
+"""
+    accs = F.queries(F.parse(text))
+    got, words = _solve(accs)
+    assert got == [1, 1, 0]
+    n, d = int(words[0][0]), int(words[0][1])
+    assert d <= n  # the witness of the first access: p1 has no room (y <= x)
+
+
+def test_use_after_free_rules():
+    text = """input n 8
+malloc a n
+malloc b n
+if n < 4
+  free a
+else
+  free b
+end
+launch k grid(1) block(1) args(a, b)
+kernel k(x, y)
+  shared s[4]
+  access s[0]
+  for i < 4
+    malloc t 8
+    free t
+  end
+  access x[0]
+end
+"""
+    uaf = F.use_after_free(F.parse(text))
+    # a and b are each freed on one branch: neither is live at the launch
+    assert sorted((u.what, u.name) for u in uaf) == sorted([("launch", "a"), ("launch", "b"),
+                                                             ("access", "x")])
+
+
+@pytest.mark.parametrize("bad", [
+    "input n 0\n",                                   # width out of range
+    "input n 8\nlet m = n +\n",                      # incomplete expression
+    "kernel k(\n",                                   # bad kernel header
+    "input n 8\nif n < 2\n",                         # unterminated block
+    "end\n",                                         # stray end
+    "input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  access q[0]\nend\n",
+    "input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  local l[4]\n  access l[x / (x)]\nend\n",
+])
+def test_malformed_programs_are_rejected(bad):
+    with pytest.raises(F.ProgramError):
+        F.queries(F.parse(bad))

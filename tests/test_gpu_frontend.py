@@ -1,0 +1,52 @@
+"""The front end on the GPU: the worked examples written as programs and the
+two query families written as programs, decided through analyze_programs
+(one batch, through the C ABI), verdicts against the cited expectations and
+the closed forms, every witness satisfying its query."""
+import glob
+import os
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from closed_forms import bounds_algebra, partition_algebra
+from ir_eval import evaluate
+from test_frontend import PROGRAMS, bounds_program, partition_program
+from workloads import queries
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def frontend():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_21552_gb300 import build
+    build.build()
+    from paper_2601_21552_gb300 import frontend as F
+    return F
+
+
+@pytest.mark.parametrize("search", ["dpll", "cdcl"])
+def test_worked_examples_as_programs(frontend, search):
+    texts = [open(p).read() for p in PROGRAMS]
+    reports = frontend.analyze_programs(texts, search=search, time_budget_ms=60000)
+    for path, rep in zip(PROGRAMS, reports):
+        for a in rep.accesses:
+            assert a.verdict == (1 if a.meta["expect"] == "SAT" else 0), (path, a.line)
+            if a.verdict == 1:
+                assert evaluate(a.ir, [a.witness[k] for k in a.inputs]), (path, a.line)
+    uaf = [(os.path.basename(p), u.what, u.name) for p, r in zip(PROGRAMS, reports)
+           for u in r.uaf]
+    assert sorted(uaf) == [("uaf_host_and_kernel.kp", "access", "p"),
+                           ("uaf_host_and_kernel.kp", "launch", "a")]
+
+
+def test_families_as_programs(frontend):
+    bp = [queries.config1_params(8400 + i, w=8) for i in range(64)]
+    pp = [queries.config2_params(8500 + i, w=8) for i in range(64)]
+    texts = [bounds_program(**p) for p in bp] + [partition_program(**p) for p in pp]
+    reports = frontend.analyze_programs(texts, bid_width=8, search="cdcl")
+    got = [r.accesses[0].verdict for r in reports]
+    want = [int(bounds_algebra(**p)) for p in bp] + [int(partition_algebra(**p)) for p in pp]
+    assert got == want
