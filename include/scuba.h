@@ -199,6 +199,31 @@ int scuba_solve_batch_ex(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t
                          void* stream, const scuba_options* opt);
 
 /*
+ * Incremental form. Within one kernel the paper's constraints of kinds 1
+ * and 3 (ids, grid dimensions, value definitions, asserts) are the same for
+ * every memory instruction and only kind 2 differs (Sec. V-B); a caller can
+ * encode a kernel once, guard each instruction's own constraints with a
+ * selector input, and decide the instructions as units: unit u is instance
+ * unit_inst[u] of `batch` under the assumption literals
+ * asm_lits[asm_begin[u] .. asm_begin[u+1]) (DIMACS, at most 248 per unit).
+ * verdict[u] = SAT iff a model of the instance makes every assumption of u
+ * true; UNSAT iff none does; UNKNOWN on a budget, time-out or error.
+ *   - All arrays are DEVICE memory owned by the caller: unit_inst i32[n_units];
+ *     asm_begin i64[n_units+1] (NULL: no assumptions), asm_lits i32;
+ *     unit_model_begin i64[n_units] (required when model != NULL: unit u's
+ *     model goes to model[unit_model_begin[u] ..] for the num_vars of its
+ *     instance; ranges must not overlap); verdict u8[n_units].
+ *   - Options as for scuba_solve_batch_ex (both searches; no trace); order,
+ *     stats and finish_ns are per unit; the budgets count per unit.
+ *   - Errors: SCUBA_ERR_ARG synchronously; an instance index or assumption
+ *     literal out of range makes that unit UNKNOWN with SCUBA_ERR_MALFORMED.
+ */
+int scuba_solve_units(const scuba_cnf_batch* batch, int32_t n_units, const int32_t* unit_inst,
+                      const int64_t* asm_begin, const int32_t* asm_lits,
+                      const int64_t* unit_model_begin, uint8_t* verdict, uint8_t* model,
+                      void* stream, const scuba_options* opt);
+
+/*
  * Same as scuba_solve_batch_ex, but every array of `batch`, `verdict`,
  * `model` and `opt->stats` is a HOST pointer. The call copies the batch to
  * library scratch on the device, solves, copies verdicts/models/stats back

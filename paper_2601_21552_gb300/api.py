@@ -187,6 +187,46 @@ def solve(db: DeviceBatch, want_model: bool = True, stats: bool = True,
         (st[:db.n] if st is not None else None)
 
 
+def solve_units(db: DeviceBatch, unit_inst, asm_begin=None, asm_lits=None,
+                want_model: bool = True, stream: torch.cuda.Stream | None = None, **opts):
+    """Launch scuba_solve_units: unit u is instance unit_inst[u] of the batch
+    under the DIMACS assumption literals asm_lits[asm_begin[u]:asm_begin[u+1]]
+    (numpy or tensors). Returns (verdict u8[n_units], model u8 | None, model
+    offset of each unit i64[n_units]) device tensors; asynchronous like
+    solve()."""
+    dev = db.icb.device
+    if opts.pop("tuned", False):
+        from . import autotune
+        tuned = autotune.load()
+        if opts.get("search") == "cdcl":
+            tuned.update(autotune.load(section="best_cdcl"))
+        for k, v in tuned.items():
+            opts.setdefault(k, v)
+    t = lambda a, dt: torch.as_tensor(np.asarray(a), dtype=dt).to(dev)
+    ui = t(unit_inst, torch.int32)
+    n_units = int(ui.numel())
+    ab = t(asm_begin, torch.int64) if asm_begin is not None else None
+    al = t(asm_lits if asm_lits is not None and len(asm_lits) else [0], torch.int32) \
+        if asm_begin is not None else None
+    nv = db.nv.to(torch.int64)[ui.long()] if n_units else torch.zeros(0, dtype=torch.int64,
+                                                                         device=dev)
+    mb = torch.zeros(max(n_units, 1), dtype=torch.int64, device=dev)
+    if n_units:
+        mb[1:n_units] = torch.cumsum(nv, 0)[:-1]
+    total = int(nv.sum().item()) if n_units else 0
+    verdict = torch.empty(max(n_units, 1), dtype=torch.uint8, device=dev)
+    model = torch.zeros(max(total, 1), dtype=torch.uint8, device=dev) if want_model else None
+    opts.setdefault("num_inputs", db.num_inputs)
+    o = options(**opts)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    B.scuba_solve_units(db.struct(), n_units, ui.data_ptr(),
+                        ab.data_ptr() if ab is not None else None,
+                        al.data_ptr() if al is not None else None,
+                        mb.data_ptr() if model is not None else None, verdict.data_ptr(),
+                        model.data_ptr() if model is not None else None, s.cuda_stream, o)
+    return verdict[:n_units], model, mb[:n_units]
+
+
 def status(stream: torch.cuda.Stream | None = None) -> int:
     s = stream if stream is not None else torch.cuda.current_stream()
     return B.scuba_sync_status(s.cuda_stream)

@@ -77,6 +77,8 @@ _sig("scuba_solve_batch_ex", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _
                                     ctypes.POINTER(scuba_options)])
 _sig("scuba_solve_batch_host", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _vp,
                                       ctypes.POINTER(scuba_options)])
+_sig("scuba_solve_units", _i32, [ctypes.POINTER(scuba_cnf_batch), _i32, _vp, _vp, _vp, _vp, _vp,
+                                 _vp, _vp, ctypes.POINTER(scuba_options)])
 _sig("scuba_solve_batch_noalloc", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _vp,
                                          ctypes.POINTER(scuba_options)])
 _sig("scuba_propagate_batch", _i32, [ctypes.POINTER(scuba_cnf_batch), _vp, _vp, _vp, _vp, _vp])
@@ -101,8 +103,9 @@ _sig("scuba_mlp_train", _i32, [ctypes.POINTER(scuba_trace), _i64, _vp, _vp, _vp,
                                _i32, ctypes.c_float, _vp, _vp])
 
 EXPORTED = [
-    "scuba_options_init", "scuba_solve_batch", "scuba_solve_batch_ex",
-    "scuba_solve_batch_host", "scuba_solve_batch_noalloc", "scuba_propagate_batch", "scuba_sync_status", "scuba_release", "scuba_last_error",
+    "scuba_options_init", "scuba_solve_batch", "scuba_solve_batch_ex", "scuba_solve_units",
+    "scuba_solve_batch_host", "scuba_solve_batch_noalloc", "scuba_propagate_batch",
+    "scuba_sync_status", "scuba_release", "scuba_last_error",
     "scuba_version", "scuba_abi_sizes", "scuba_encode_batch", "scuba_encoded_sizes", "scuba_encoded_copy",
     "scuba_encoded_inputs", "scuba_encoded_free", "scuba_encoded_release_clauses",
     "scuba_verify_batch",
@@ -269,6 +272,17 @@ def scuba_solve_batch_noalloc(batch: scuba_cnf_batch, verdict_ptr: int, model_pt
     return _check(_lib.scuba_solve_batch_noalloc(ctypes.byref(batch), verdict_ptr, model_ptr,
                                                  stream_ptr, ctypes.byref(opt)),
                   "scuba_solve_batch_noalloc")
+
+
+def scuba_solve_units(batch: scuba_cnf_batch, n_units: int, unit_inst_ptr, asm_begin_ptr,
+                      asm_lits_ptr, unit_model_begin_ptr, verdict_ptr, model_ptr, stream_ptr,
+                      opt: scuba_options | None = None) -> int:
+    if opt is None:
+        opt = scuba_options_init()
+    return _check(_lib.scuba_solve_units(ctypes.byref(batch), int(n_units), unit_inst_ptr,
+                                         asm_begin_ptr, asm_lits_ptr, unit_model_begin_ptr,
+                                         verdict_ptr, model_ptr, stream_ptr, ctypes.byref(opt)),
+                  "scuba_solve_units")
 
 
 def scuba_sync_status(stream_ptr=None) -> int:

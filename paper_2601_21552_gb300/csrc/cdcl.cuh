@@ -937,8 +937,8 @@ __device__ uint32_t pick_cd(Warp& w) {
 // One job: an instance, or a cube of it (the job's literals as assumptions,
 // from the subtree-sharing ring), start to verdict. Returns SAT, UNSAT (for a
 // cube: no model extends it) or UNKNOWN.
-__device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const TakenJob* job,
-                        uint2* ring, int& abort_code) {
+__device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int inst,
+                        const TakenJob* job, uint2* ring, int& abort_code) {
   CdWarp cd;
   cd.ring = ring;
   cd.cand = ring + RING;
@@ -1013,7 +1013,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
       if (w.lane == 0) {
         if (S.abort_flag && *S.abort_flag) stop = 1;
         else if (globaltimer() - S.ctrl->t0 > S.time_ns) stop = 2;
-        else if (*(volatile uint32_t*)&S.done[inst] & 1u) stop = 3;
+        else if (*(volatile uint32_t*)&S.done[unit] & 1u) stop = 3;
       }
       stop = __shfl_sync(FULL, stop, 0);
       if (stop == 1) { abort_code = SCUBA_ERR_ABORTED; return SCUBA_UNKNOWN; }
@@ -1068,7 +1068,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
       pf_add(S, w, PF_ANALYZE, t0);
       if (S.budget > 0) {  // conflicts of the instance, all of its cubes together
         unsigned long long tot = 0;
-        if (w.lane == 0) tot = atomicAdd(&S.inst_dec[inst], 1ull) + 1ull;
+        if (w.lane == 0) tot = atomicAdd(&S.inst_dec[unit], 1ull) + 1ull;
         tot = __shfl_sync(FULL, tot, 0);
         if ((int64_t)tot >= S.budget) return SCUBA_UNKNOWN;
       }
@@ -1094,11 +1094,12 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
     if (v == NONE) {
       // the first cube of the instance to reach a model writes it
       uint32_t won = 0;
-      if (w.lane == 0) won = !(atomicOr(&S.done[inst], 8u) & 8u);
+      if (w.lane == 0) won = !(atomicOr(&S.done[unit], 8u) & 8u);
       won = __shfl_sync(FULL, won, 0);
       if (won && S.model)
         for (uint32_t x = w.lane; x < w.V; x += 32) {
-          S.model[S.vb[inst] + x] = (nib(w.asg, x) & 3u) == NB_T ? 1 : 0;
+          S.model[(S.unit_vb ? S.unit_vb[unit] : S.vb[inst]) + x] =
+              (nib(w.asg, x) & 3u) == NB_T ? 1 : 0;
         }
       __syncwarp();
       return SCUBA_SAT;
@@ -1113,9 +1114,9 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
       idle = __shfl_sync(FULL, idle, 0);
       if (idle > 0) {
         const uint32_t k = w.nd_fixed;
-        if (w.lane == 0) atomicAdd(&S.pending[inst], 1u);
+        if (w.lane == 0) atomicAdd(&S.pending[unit], 1u);
         __syncwarp();
-        if (ring_push(S, w, inst, k + 1, w.trail, w.dstack, k, [&](uint32_t cell) {
+        if (ring_push(S, w, unit, k + 1, w.trail, w.dstack, k, [&](uint32_t cell) {
               export_clauses(w, cd, S.job_cls + (size_t)cell * JOB_CLS_WORDS);
             })) {
           w.nd_fixed = k + 1;
@@ -1128,7 +1129,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int inst, const T
             }
           }
         } else if (w.lane == 0) {
-          atomicSub(&S.pending[inst], 1u);
+          atomicSub(&S.pending[unit], 1u);
           if (S.prof) atomicAdd(&S.prof[4], 1ull);
         }
         __syncwarp();

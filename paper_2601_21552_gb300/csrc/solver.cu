@@ -373,6 +373,13 @@ struct Solve {
   const uint32_t* nunits;
   const uint32_t* flags;
   const int32_t* order;
+  // units: instance + assumption literals (solve_units); without a unit table
+  // every instance is one unit with no assumptions
+  int n_units;
+  const int32_t* unit_inst;        // [n_units] or NULL (unit u is instance u)
+  const int64_t* unit_asm_begin;   // [n_units+1] or NULL
+  const int32_t* unit_asm;         // DIMACS assumption literals
+  const int64_t* unit_vb;          // [n_units] model offset of each unit, or NULL
   uint8_t* verdict;
   uint8_t* model;
   int64_t* stats;
@@ -1011,22 +1018,23 @@ __device__ void ring_release(const Solve& S, uint32_t slot, int lane) {
   __syncwarp();
 }
 
-// An instance's job finished with result r (SCUBA_SAT / SCUBA_UNSAT /
-// SCUBA_UNKNOWN). The last open job of an instance writes its verdict.
-__device__ void finish_job(const Solve& S, Warp& w, int inst, int r) {
+// A unit's job finished with result r (SCUBA_SAT / SCUBA_UNSAT /
+// SCUBA_UNKNOWN). The last open job of a unit (an instance, or an instance
+// under assumptions) writes its verdict.
+__device__ void finish_job(const Solve& S, Warp& w, int unit, int r) {
   if (w.lane == 0) {
     if (r == SCUBA_SAT) {
-      S.verdict[inst] = SCUBA_SAT;
-      atomicOr(&S.done[inst], 1u);
+      S.verdict[unit] = SCUBA_SAT;
+      atomicOr(&S.done[unit], 1u);
     } else if (r == SCUBA_UNKNOWN) {
-      atomicOr(&S.done[inst], 2u);  // mark: some subtree gave up
+      atomicOr(&S.done[unit], 2u);  // mark: some subtree gave up
     }
-    uint32_t left = atomicSub(&S.pending[inst], 1u) - 1u;
+    uint32_t left = atomicSub(&S.pending[unit], 1u) - 1u;
     if (left == 0u) {
-      uint32_t d = atomicOr(&S.done[inst], 4u);
-      if (!(d & 1u)) S.verdict[inst] = (d & 2u) ? SCUBA_UNKNOWN : SCUBA_UNSAT;
+      uint32_t d = atomicOr(&S.done[unit], 4u);
+      if (!(d & 1u)) S.verdict[unit] = (d & 2u) ? SCUBA_UNKNOWN : SCUBA_UNSAT;
       atomicSub(&S.ctrl->inst_left, 1u);
-      if (S.finish_ns) S.finish_ns[inst] = (int64_t)(globaltimer() - S.ctrl->t0);
+      if (S.finish_ns) S.finish_ns[unit] = (int64_t)(globaltimer() - S.ctrl->t0);
     }
     if (S.prof) {
       atomicAdd(&S.prof[1], 1ull);  // jobs run
@@ -1034,7 +1042,7 @@ __device__ void finish_job(const Solve& S, Warp& w, int inst, int r) {
         if (w.ws->cyc[k]) atomicAdd(&S.prof[8 + k], w.ws->cyc[k]);
     }
     if (S.stats) {
-      unsigned long long* st = (unsigned long long*)&S.stats[SCUBA_NSTATS * (int64_t)inst];
+      unsigned long long* st = (unsigned long long*)&S.stats[SCUBA_NSTATS * (int64_t)unit];
       atomicAdd(st + 0, w.ws->decisions);
       atomicAdd(st + 1, w.ws->conflicts);
       atomicAdd(st + 2, w.ws->props);
@@ -1057,13 +1065,38 @@ struct TakenJob {
 };
 
 template <int MODE>
-__device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* job,
+__device__ int run_job_body(const Solve& S, Warp& w, int unit, int inst, const TakenJob* job,
                             int& abort_code);
+
+// A unit's assumption literals as the job of a fresh search (all lanes):
+// converted into the slot's prefix buffer, activities zeroed. Returns true
+// if a literal is out of range or there are more than MAX_PREFIX of them.
+__device__ __noinline__ bool unit_job(const Solve& S, int unit, int inst, int64_t slot, int lane,
+                                      float* act, TakenJob* out) {
+  const int64_t ab = S.unit_asm_begin[unit], ae = S.unit_asm_begin[unit + 1];
+  const int32_t V = min(S.nv[inst], S.vmax);
+  bool bad = ae - ab > MAX_PREFIX;
+  uint32_t* pre = S.prefix + slot * MAX_PREFIX;
+  for (int64_t q = ab + lane; !bad && q < ae; q += 32) {
+    const int32_t l = S.unit_asm[q];
+    if (l == 0 || l > V || l < -V) bad = true;
+    else pre[q - ab] = code_of(l);
+  }
+  bad = __any_sync(FULL, bad);
+  for (int v = lane; v < V; v += 32) act[v] = 0.0f;  // fresh activities
+  out->lit = pre;
+  out->len = (int32_t)(ae - ab < MAX_PREFIX ? ae - ab : MAX_PREFIX);
+  out->inc = 1.0f;
+  out->cls = nullptr;
+  __syncwarp();
+  return bad;
+}
 
 // Runs one job; in trace mode every level still open at the end is closed.
 template <int MODE>
-__device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, int& abort_code) {
-  const int r = run_job_body<MODE>(S, w, inst, job, abort_code);
+__device__ int run_job(const Solve& S, Warp& w, int unit, int inst, const TakenJob* job,
+                       int& abort_code) {
+  const int r = run_job_body<MODE>(S, w, unit, inst, job, abort_code);
   if (MODE == MODE_TRACE) {
     const uint32_t hi_l = min(w.nd, (uint32_t)S.trace_depth);
     for (uint32_t l = 0; l < hi_l; l++) trace_close(w, l);
@@ -1072,7 +1105,7 @@ __device__ int run_job(const Solve& S, Warp& w, int inst, const TakenJob* job, i
 }
 
 template <int MODE>
-__device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* job,
+__device__ int run_job_body(const Solve& S, Warp& w, int unit, int inst, const TakenJob* job,
                             int& abort_code) {
   w.inst = inst;
   w.V = (uint32_t)S.nv[inst];
@@ -1127,7 +1160,7 @@ __device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* j
       if (w.lane == 0) {
         if (S.abort_flag && *S.abort_flag) stop = 1;
         else if (globaltimer() - S.ctrl->t0 > S.time_ns) stop = 2;
-        else if (*(volatile uint32_t*)&S.done[inst] & 1u) stop = 3;  // solved elsewhere
+        else if (*(volatile uint32_t*)&S.done[unit] & 1u) stop = 3;  // solved elsewhere
       }
       stop = __shfl_sync(FULL, stop, 0);
       if (stop == 1) { abort_code = SCUBA_ERR_ABORTED; return SCUBA_UNKNOWN; }
@@ -1148,12 +1181,12 @@ __device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* j
     if (v == NONE) {
       // the first subtree of the instance to reach a model writes it
       uint32_t won = 0;
-      if (w.lane == 0) won = !(atomicOr(&S.done[inst], 8u) & 8u);
+      if (w.lane == 0) won = !(atomicOr(&S.done[unit], 8u) & 8u);
       won = __shfl_sync(FULL, won, 0);
       if (won && S.model)
         for (uint32_t x = w.lane; x < w.V; x += 32) {
           uint32_t bits = (w.asg[x >> 4] >> ((x & 15u) * 2u)) & 3u;
-          S.model[S.vb[inst] + x] = bits == 1u ? 1 : 0;
+          S.model[(S.unit_vb ? S.unit_vb[unit] : S.vb[inst]) + x] = bits == 1u ? 1 : 0;
         }
       __syncwarp();
       return SCUBA_SAT;
@@ -1161,7 +1194,7 @@ __device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* j
     // budget: decisions of the instance across all of its subtrees
     if (S.budget > 0 && (w.decisions & 255) == 0) {
       unsigned long long tot = 0;
-      if (w.lane == 0) tot = atomicAdd(&S.inst_dec[inst], 256ull);
+      if (w.lane == 0) tot = atomicAdd(&S.inst_dec[unit], 256ull);
       tot = __shfl_sync(FULL, tot, 0);
       if ((int64_t)tot >= S.budget) return SCUBA_UNKNOWN;
     }
@@ -1177,9 +1210,9 @@ __device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* j
           while (k < w.nd && (w.dstack[k] & FLIP)) k++;
         k = __shfl_sync(FULL, k, 0);
         if (k < w.nd && k + 1 <= (uint32_t)MAX_PREFIX) {
-          if (w.lane == 0) atomicAdd(&S.pending[inst], 1u);
+          if (w.lane == 0) atomicAdd(&S.pending[unit], 1u);
           __syncwarp();
-          if (ring_push(S, w, inst, k + 1, w.trail, w.dstack, k)) {
+          if (ring_push(S, w, unit, k + 1, w.trail, w.dstack, k)) {
             if (w.lane == 0) {
               w.dstack[k] |= FLIP;
               atomicAdd(&S.ctrl->jobs_split, 1u);
@@ -1190,7 +1223,7 @@ __device__ int run_job_body(const Solve& S, Warp& w, int inst, const TakenJob* j
               }
             }
           } else if (w.lane == 0) {
-            atomicSub(&S.pending[inst], 1u);
+            atomicSub(&S.pending[unit], 1u);
             if (S.prof) atomicAdd(&S.prof[4], 1ull);  // ring full
           }
           __syncwarp();
@@ -1272,15 +1305,18 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
   if (batch_failed(S.ctrl)) return;
   bool counted_idle = false;
   for (;;) {
-    // 1) a shared subtree, 2) a fresh instance, 3) wait for shared work
-    int inst = -1;
+    // 1) a shared subtree, 2) a fresh unit (an instance, possibly under
+    // assumptions), 3) wait for shared work
+    int inst = -1, unit = -1;
+    bool bad_unit = false;
     uint32_t slot_j = ring_pop(S, lane);
     TakenJob taken;
     const TakenJob* job = nullptr;
     if (slot_j != NONE) {
       // copy the cell out (prefix, activity snapshot) and release it at once
       const Job* cell = &S.ring[slot_j & (S.ring_cap - 1)];
-      inst = cell->inst;
+      unit = cell->inst;
+      inst = S.unit_inst ? S.unit_inst[unit] : unit;
       const int32_t len = cell->len;
       uint32_t* pre = S.prefix + slot * MAX_PREFIX;
       for (int k = lane; k < len; k += 32) pre[k] = cell->lit[k];
@@ -1305,8 +1341,17 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
       uint32_t k = 0;
       if (lane == 0) k = atomicAdd(&S.ctrl->next_inst, 1u);
       k = __shfl_sync(FULL, k, 0);
-      if (k < (uint32_t)S.n) {
-        inst = S.order ? S.order[k] : (int)k;
+      if (k < (uint32_t)S.n_units) {
+        unit = S.order ? S.order[k] : (int)k;
+        inst = S.unit_inst ? S.unit_inst[unit] : unit;
+        if (inst < 0 || inst >= S.n) {
+          bad_unit = true;
+          inst = 0;
+        } else if (S.unit_asm_begin &&
+                   S.unit_asm_begin[unit + 1] > S.unit_asm_begin[unit]) {
+          bad_unit = unit_job(S, unit, inst, slot, lane, w.act, &taken);
+          job = &taken;
+        }
       } else {
         if (!counted_idle) {
           if (lane == 0) atomicAdd(&S.ctrl->idle, 1u);
@@ -1342,9 +1387,12 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
     }
     __syncwarp();
     uint32_t moot = 0;
-    if (lane == 0) moot = *(volatile uint32_t*)&S.done[inst] & 1u;
+    if (lane == 0) moot = *(volatile uint32_t*)&S.done[unit] & 1u;
     moot = __shfl_sync(FULL, moot, 0);
-    if (S.flags[inst] & F_BAD) {
+    if (bad_unit) {  // an instance index or assumption literal out of range
+      r = SCUBA_UNKNOWN;
+      if (lane == 0) set_status(S, SCUBA_ERR_MALFORMED);
+    } else if (S.flags[inst] & F_BAD) {
       r = SCUBA_UNKNOWN;
       if (lane == 0) set_status(S, SCUBA_ERR_MALFORMED);
     } else if (S.nv[inst] > S.vmax) {
@@ -1353,11 +1401,11 @@ __global__ void __launch_bounds__(256, MODE == MODE_LEARNED ? SCUBA_LEARNED_MINB
     } else if (moot) {
       r = SCUBA_UNSAT;  // moot: another subtree already found a model
     } else if constexpr (MODE == MODE_CDCL) {
-      r = run_cdcl(S, w, slot, inst, job, ring, abort_code);
+      r = run_cdcl(S, w, slot, unit, inst, job, ring, abort_code);
     } else {
-      r = run_job<MODE>(S, w, inst, job, abort_code);
+      r = run_job<MODE>(S, w, unit, inst, job, abort_code);
     }
-    finish_job(S, w, inst, r);
+    finish_job(S, w, unit, r);
     if (abort_code) {
       if (lane == 0) set_status(S, abort_code);
       break;
@@ -1445,7 +1493,8 @@ __global__ void __launch_bounds__(256) k_propagate(const __grid_constant__ PropA
 
 // Instances still open when the kernel stopped (timeout / abort) -> UNKNOWN.
 __global__ void k_finalize(Solve S) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n_units;
+       i += gridDim.x * blockDim.x) {
     uint32_t d = S.done[i];
     if (!(d & 5u)) S.verdict[i] = SCUBA_UNKNOWN;
   }
@@ -1560,8 +1609,18 @@ extern "C" int scuba_options_init(scuba_options* o) {
   return SCUBA_OK;
 }
 
+// Units for scuba_solve_units: unit u is instance inst[u] under the
+// assumption literals asm_lits[asm_begin[u] .. asm_begin[u+1]).
+struct UnitArgs {
+  int32_t n;
+  const int32_t* inst;
+  const int64_t* asm_begin;
+  const int32_t* asm_lits;
+  const int64_t* model_begin;
+};
+
 static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model,
-                      cudaStream_t st, const scuba_options* opt) {
+                      cudaStream_t st, const scuba_options* opt, const UnitArgs* ua = nullptr) {
   if (!b || b->num_instances < 0 || b->total_clauses < 0 || b->total_lits < 0 ||
       b->max_vars < 0 || b->total_vars < 0) {
     set_error("scuba_solve_batch: bad arguments");
@@ -1571,7 +1630,12 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   scuba_options_init(&defaults);
   if (!opt) opt = &defaults;
   const int n = b->num_instances;
-  if (n == 0) return SCUBA_OK;
+  const int n_units = ua ? ua->n : n;
+  if (n_units == 0) return SCUBA_OK;
+  if (n == 0 || n_units < 0 || (ua && (!ua->inst || (ua->asm_begin && !ua->asm_lits)))) {
+    set_error("scuba_solve_units: units need instances, a unit table and assumption literals");
+    return SCUBA_ERR_ARG;
+  }
   if (!verdict) {
     set_error("scuba_solve_batch: NULL verdict array");
     return SCUBA_ERR_ARG;
@@ -1607,6 +1671,10 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
         T->max_rows < 0 || !T->counts || !T->node_inst || !T->node_depth || !T->node_row ||
         !T->node_nrows || !T->node_closed || !T->x || !T->target || !T->var) {
       set_error("scuba_solve_batch: bad trace buffers (depth 1..8, all arrays set)");
+      return SCUBA_ERR_ARG;
+    }
+    if (ua) {
+      set_error("scuba_solve_units: trace recording takes whole instances");
       return SCUBA_ERR_ARG;
     }
     mode = dev::MODE_TRACE;
@@ -1669,8 +1737,8 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
       ensure(S.occ_cnt, 4 * (size_t)occ_total) || ensure(S.occ_begin, 4 * (size_t)occ_total) ||
       ensure(S.ent, 8 * (size_t)L) || ensure(S.units, 4 * (size_t)std::max<int64_t>(C, 1)) ||
       ensure(S.nunits, 4 * (size_t)n) || ensure(S.flags, 4 * (size_t)n) ||
-      ensure(S.pending, 4 * (size_t)n) || ensure(S.done, 4 * (size_t)n) ||
-      ensure(S.inst_dec, 8 * (size_t)n) || ensure(S.trail, 4 * (size_t)slots * vmax) ||
+      ensure(S.pending, 4 * (size_t)n_units) || ensure(S.done, 4 * (size_t)n_units) ||
+      ensure(S.inst_dec, 8 * (size_t)n_units) || ensure(S.trail, 4 * (size_t)slots * vmax) ||
       ensure(S.dstack, 4 * (size_t)slots * vmax) || ensure(S.act, 4 * (size_t)slots * vmax) ||
       ensure(S.ring, sizeof(dev::Job) * (size_t)ring_cap) ||
       ensure(S.job_act, 4 * (size_t)ring_cap * vmax) ||
@@ -1728,7 +1796,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   pr.vb = b->inst_var_begin;
   pr.ctrl = P<dev::Ctrl>(S.ctrl);
 
-  dev::k_init_ctrl<<<1, 1, 0, st>>>(pr.ctrl, (uint32_t)n);
+  dev::k_init_ctrl<<<1, 1, 0, st>>>(pr.ctrl, (uint32_t)n_units);
   cudaMemsetAsync(pr.occ_cnt, 0, 4 * (size_t)occ_total, st);
   cudaMemsetAsync(pr.flags, 0, 4 * (size_t)n, st);
   dev::k_occ_base<<<1, 1024, 0, st>>>(pr);
@@ -1756,6 +1824,11 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.nunits = pr.nunits;
   sv.flags = pr.flags;
   sv.order = opt->order;
+  sv.n_units = n_units;
+  sv.unit_inst = ua ? ua->inst : nullptr;
+  sv.unit_asm_begin = ua ? ua->asm_begin : nullptr;
+  sv.unit_asm = ua ? ua->asm_lits : nullptr;
+  sv.unit_vb = ua ? ua->model_begin : nullptr;
   sv.verdict = verdict;
   sv.model = model;
   sv.stats = opt->stats;
@@ -1823,7 +1896,8 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   }
 
   dev::k_init_ring<<<16, 256, 0, st>>>(sv.ring, ring_cap);
-  dev::k_init_inst<<<(n + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec, n);
+  dev::k_init_inst<<<(n_units + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec,
+                                                          n_units);
   dev::k_start_clock<<<1, 1, 0, st>>>(sv.ctrl);
   auto kern = mode == dev::MODE_TRACE     ? dev::k_solve<dev::MODE_TRACE>
               : mode == dev::MODE_LEARNED ? dev::k_solve<dev::MODE_LEARNED>
@@ -1840,7 +1914,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   if (opt->search_event_begin) cudaEventRecord((cudaEvent_t)opt->search_event_begin, st);
   kern<<<S.sms * bps, 32 * wpb, smem, st>>>(sv);
   if (opt->search_event_end) cudaEventRecord((cudaEvent_t)opt->search_event_end, st);
-  dev::k_finalize<<<(n + 255) / 256, 256, 0, st>>>(sv);
+  dev::k_finalize<<<(n_units + 255) / 256, 256, 0, st>>>(sv);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail("kernel launch", e);
   return SCUBA_OK;
@@ -1849,6 +1923,19 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
 extern "C" int scuba_solve_batch_ex(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model,
                                     void* stream, const scuba_options* opt) {
   return solve_impl(b, verdict, model, (cudaStream_t)stream, opt);
+}
+
+extern "C" int scuba_solve_units(const scuba_cnf_batch* b, int32_t n_units,
+                                 const int32_t* unit_inst, const int64_t* asm_begin,
+                                 const int32_t* asm_lits, const int64_t* unit_model_begin,
+                                 uint8_t* verdict, uint8_t* model, void* stream,
+                                 const scuba_options* opt) {
+  if (n_units < 0 || (n_units > 0 && (!unit_inst || !verdict)) || (model && !unit_model_begin)) {
+    set_error("scuba_solve_units: bad arguments");
+    return SCUBA_ERR_ARG;
+  }
+  UnitArgs ua{n_units, unit_inst, asm_begin, asm_lits, unit_model_begin};
+  return solve_impl(b, verdict, model, (cudaStream_t)stream, opt, &ua);
 }
 
 extern "C" int scuba_solve_batch(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model,
@@ -2103,6 +2190,7 @@ extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verd
   sv.units = pr.units;
   sv.nunits = pr.nunits;
   sv.flags = pr.flags;
+  sv.n_units = n;
   sv.order = opt->order;
   sv.verdict = verdict;
   sv.model = model;

@@ -718,6 +718,101 @@ def _kernel_path(b, kenv, sizes, shared, stmts, target, state):
     return False
 
 
+def _kernel_all(b, kenv, sizes, shared, stmts, conds, parts, out):
+    """One walk over the kernel for the incremental form: every memory
+    instruction gets the conjunction of the path conditions, loop bounds and
+    asserts that hold at it, and its kind-2 constraint, as one Boolean
+    (appended to out with the statement)."""
+    kenv, sizes, parts = dict(kenv), dict(sizes), {k: list(v) for k, v in parts.items()}
+    conds = list(conds)
+    for st in stmts:
+        a = st.args
+        if st.kind == "let":
+            kenv[a["name"]] = _eval(b, kenv, a["expr"], st.line)
+        elif st.kind == "input":
+            kenv[a["name"]] = (b.free(a["width"], a["name"]), 0)
+        elif st.kind in ("static", "malloc"):
+            sizes[a["name"]] = _eval(b, kenv, a["expr"], st.line)
+            kenv[a["name"]] = None
+        elif st.kind == "dynshared":
+            parts[a["name"]] = [(a["name"], (0, 0))]
+            kenv[a["name"]] = None
+        elif st.kind == "partition":
+            base = a["base"]
+            if base not in parts:
+                if base not in sizes:
+                    raise ProgramError(f"line {st.line}: partition of an unknown allocation")
+                parts[base] = [(base, (0, 0))]
+            parts[base].append((a["name"], _eval(b, kenv, a["expr"], st.line)))
+            kenv[a["name"]] = None
+        elif st.kind == "assert":
+            conds.append(_eval_bool(b, kenv, a["cond"], st.line))
+        elif st.kind == "if":
+            c = _eval_bool(b, kenv, a["cond"], st.line)
+            _kernel_all(b, kenv, sizes, shared, st.body, conds + [c], parts, out)
+            _kernel_all(b, kenv, sizes, shared, st.orelse, conds + [b.bnot(c)], parts, out)
+        elif st.kind == "for":
+            bound = _eval(b, kenv, a["bound"], st.line)
+            v = (b.free(_bits(b.vmax(bound[0])), a["var"]), 0)
+            inner = dict(kenv)
+            inner[a["var"]] = v
+            _kernel_all(b, inner, sizes, shared, st.body, conds + [b.less(v, bound)], parts, out)
+        elif st.kind == "access":
+            ptr = a["ptr"]
+            psize = {}
+            for base, chain in parts.items():
+                end = shared if base not in sizes else sizes[base]
+                psize.update(_partition_sizes(b, chain, end, st.line))
+            size = psize.get(ptr, sizes.get(ptr))
+            if size is None:
+                raise ProgramError(f"line {st.line}: {ptr!r} is not a known allocation")
+            off = _eval(b, kenv, a["expr"], st.line)
+            oob = b.less(size, off, strict=False)
+            if isinstance(off[1], _N) or off[1] != 0:
+                oob = b.bor(oob, b.less(off, (0, 0)))
+            for c in conds:
+                oob = b.band(c, oob)
+            out.append((st, oob))
+
+
+@dataclass
+class KernelQuery:
+    """The incremental form of one kernel: one query holding the shared
+    constraints (kinds 1 and 3 of Sec. V-B) and, per memory instruction, its
+    own constraints guarded by a one-bit selector input (selector -> its
+    constraints). Solving with selector k assumed true decides access k."""
+    kernel: str
+    ir: np.ndarray
+    accesses: list       # Access entries (ir None): the instructions, in program order
+    selectors: list      # FREE-word ordinal of each access's selector
+    inputs: list         # names of the FREE words
+
+
+def kernel_queries(prog: Program, bid_width: int = 16) -> list:
+    out = []
+    launched = {st.args["kernel"] for st in _flat(prog.host) if st.kind == "launch"}
+    for kname, kern in prog.kernels.items():
+        if kname not in launched:
+            continue
+        b = _Builder()
+        env, allocs, launch = _host_env(b, prog, kname, bid_width)
+        kenv, sizes, shared = _kernel_env(b, env, allocs, launch, kern, bid_width)
+        found = []
+        _kernel_all(b, kenv, sizes, shared, kern.body, [], {}, found)
+        sels = []
+        for k, (st, cond) in enumerate(found):
+            sel = b.free(1, f"@select{k}")
+            b.require(b.bor(b.bnot(b.less((0, 0), (sel, 0))), cond))
+            sels.append(sel)
+        frees = [j for j, nd in enumerate(b.ir.nodes) if nd[0] == OP.FREE]
+        names = [b.ir.names.get(j, f"free{k}") for k, j in enumerate(frees)]
+        ordinals = [frees.index(sel.i) for sel in sels]
+        accs = [Access(kname, k, st.line, st.args["ptr"], st.meta, None, names)
+                for k, (st, _c) in enumerate(found)]
+        out.append(KernelQuery(kname, b.ir.to_array(), accs, ordinals, names))
+    return out
+
+
 def _contains(stmts, target) -> bool:
     return any(st is target for st in _flat(stmts))
 
@@ -842,6 +937,62 @@ def analyze_programs(texts: list, device: str = "cuda", bid_width: int = 16,
             a.verdict = int(v)
             a.witness = dict(zip(a.inputs, wd)) if wd is not None else None
     return [Report(accs, use_after_free(p)) for p, accs in zip(progs, per)]
+
+
+def analyze_incremental(texts: list, device: str = "cuda", bid_width: int = 16,
+                        **solve_opts) -> list:
+    """Like analyze_programs, but one query per kernel: its shared constraints
+    are encoded and uploaded once, and every memory instruction is a unit of
+    scuba_solve_units with its selector assumed true. Models are re-verified
+    on the host, unit by unit."""
+    import torch
+
+    from . import api, binding as B
+
+    progs = [parse(t) for t in texts]
+    kqs = [kernel_queries(p, bid_width=bid_width) for p in progs]
+    flat = [kq for ks in kqs for kq in ks]
+    if flat:
+        enc = B.scuba_encode_batch([kq.ir for kq in flat])
+        db = api.DeviceBatch(enc, device)
+        iib, widths, var = enc.inputs()
+        bit0 = np.concatenate([[0], np.cumsum(widths)]).astype(np.int64)
+        unit_inst, asm = [], []
+        for i, kq in enumerate(flat):
+            for s in kq.selectors:
+                unit_inst.append(i)
+                asm.append(int(var[bit0[iib[i] + s]]))  # the selector's variable, true
+        asm_begin = np.arange(len(asm) + 1, dtype=np.int64)
+        v, m, mb = api.solve_units(db, unit_inst, asm_begin, np.array(asm, np.int32),
+                                   **solve_opts)
+        rc = api.status()
+        if rc != 0:
+            raise RuntimeError(f"solve failed: status {rc}")
+        vh, mh, mbh = v.cpu().numpy(), m.cpu().numpy(), mb.cpu().numpy()
+        nvs, vbs = enc.inst_num_vars, enc.inst_var_begin
+        u = 0
+        for i, kq in enumerate(flat):
+            for a in kq.accesses:
+                a.verdict = int(vh[u])
+                a.witness = None
+                if a.verdict == 1:
+                    # this unit's model in the batch's layout, checked against the IR
+                    full = np.zeros(max(int(vbs[-1]), 1), np.uint8)
+                    full[vbs[i]:vbs[i] + nvs[i]] = mh[mbh[u]:mbh[u] + nvs[i]]
+                    ver = np.full(len(flat), 2, np.uint8)
+                    ver[i] = 1
+                    fails, _ok = B.scuba_verify_batch(enc, ver, full)
+                    if fails:
+                        raise RuntimeError(f"unit {u}: the model fails the query")
+                    words = _input_words(enc, full, ver)[i]
+                    a.witness = {k: x for k, x in zip(kq.inputs, words)
+                                 if not k.startswith("@select")}
+                u += 1
+        torch.cuda.synchronize()
+    reports, k = [], 0
+    for p, ks in zip(progs, kqs):
+        reports.append(Report([a for kq in ks for a in kq.accesses], use_after_free(p)))
+    return reports
 
 
 def analyze(text: str, device: str = "cuda", bid_width: int = 16, **solve_opts) -> Report:

@@ -7,6 +7,7 @@ malformed programs."""
 import glob
 import os
 
+import numpy as np
 import pytest
 
 import oracle
@@ -169,3 +170,66 @@ end
 def test_malformed_programs_are_rejected(bad):
     with pytest.raises(F.ProgramError):
         F.queries(F.parse(bad))
+
+
+# ---------------------------------------------------------------------------
+# Incremental form: one query per kernel, a selector per memory instruction
+# ---------------------------------------------------------------------------
+
+def force_selector(ir_array, kq, k):
+    """The kernel query with access k's selector asserted true (what the
+    solver's assumption does), as a plain query for the oracle."""
+    from workloads.ir import OP, decode
+    nodes, roots = decode(ir_array)
+    frees = [j for j, nd in enumerate(nodes) if nd[0] == OP.FREE]
+    n = len(nodes)
+    nodes = nodes + [(OP.CONST, 1, 0), (OP.EQ, frees[kq.selectors[k]], n)]
+    roots = roots + [n + 1]
+    a = np.zeros(4 + 4 * len(nodes) + len(roots), np.int64)
+    a[:4] = ir_array[:4]
+    a[2], a[3] = len(nodes), len(roots)
+    a[4:4 + 4 * len(nodes)].reshape(-1, 4)[:, :3] = np.array(nodes, np.int64)
+    a[4 + 4 * len(nodes):] = roots
+    return a
+
+
+def stencil_program(w=8, radius=3):
+    """A kernel with many accesses sharing its ids, sizes and guards: a 1-D
+    stencil reading idx-r .. idx+r of an allocation of n elements under
+    the guard r <= idx < n - r, plus unguarded neighbours."""
+    acc = "\n".join(f"    access a[idx + {d}]" if d >= 0 else f"    access a[idx - {-d}]"
+                    for d in range(-radius, radius + 1))
+    return f"""input n {w}
+input bd {w}
+malloc buf n
+launch stencil grid((n + 63) / 64) block(bd) args(buf, n)
+kernel stencil(a, m)
+  let idx = blockIdx.x * blockDim.x + threadIdx.x
+  if idx >= {radius} && idx + {radius} < m
+{acc}
+  end
+  access a[idx + {radius}]
+  if idx < m
+    access a[idx]
+    access a[m - idx - 1]
+  end
+end
+"""
+
+
+@pytest.mark.parametrize("path", PROGRAMS + ["stencil"], ids=lambda p: os.path.basename(p))
+def test_incremental_form_matches_per_access(path):
+    text = stencil_program() if path == "stencil" else open(path).read()
+    prog = F.parse(text)
+    per = F.queries(prog)
+    want, _ = _solve(per)
+    forced = [force_selector(kq.ir, kq, k) for kq in F.kernel_queries(prog)
+              for k in range(len(kq.selectors))]
+    got = [int(v) for v in oracle.solve_queries(forced)["verdict"]]
+    assert got == want
+    if path == "stencil":
+        assert 0 in got and 1 in got
+        # the shared constraints are encoded once instead of once per access
+        one = sum(oracle.encode(kq.ir).nclauses for kq in F.kernel_queries(prog))
+        each = sum(oracle.encode(a.ir).nclauses for a in per)
+        assert one * 3 < each, (one, each)  # 10 accesses: 3,310 vs 12,732 clauses

@@ -50,3 +50,20 @@ def test_families_as_programs(frontend):
     got = [r.accesses[0].verdict for r in reports]
     want = [int(bounds_algebra(**p)) for p in bp] + [int(partition_algebra(**p)) for p in pp]
     assert got == want
+
+
+@pytest.mark.parametrize("search", ["dpll", "cdcl"])
+def test_incremental_form(frontend, search):
+    """One query per kernel, one unit per memory instruction (scuba_solve_units):
+    the same verdicts as the per-access queries, models verified by the host."""
+    from test_frontend import stencil_program
+    texts = [open(p).read() for p in PROGRAMS] + [stencil_program(), stencil_program(w=10, radius=5)]
+    inc = frontend.analyze_incremental(texts, search=search, time_budget_ms=60000)
+    per = frontend.analyze_programs(texts, search=search, time_budget_ms=60000)
+    for ri, rp in zip(inc, per):
+        assert [a.verdict for a in ri.accesses] == [a.verdict for a in rp.accesses]
+        assert [(u.what, u.name) for u in ri.uaf] == [(u.what, u.name) for u in rp.uaf]
+        for a in ri.accesses:
+            assert (a.witness is not None) == (a.verdict == 1)
+    flat = [a.verdict for r in inc for a in r.accesses]
+    assert 0 in flat and 1 in flat
