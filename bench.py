@@ -42,12 +42,12 @@ WORKLOAD = "partition queries, 16-bit inputs (4,096 per GPU)"
 
 
 # DRAM traffic of the clause-learning search kernel from one single-pass ncu
-# capture of a full launch (profiles/k_solve_cdcl_partition16.md: 6.69 GB read +
-# 5.27 GB written for 1.480e8 propagations), per propagation, valid only for
+# capture of a full launch (profiles/k_solve_cdcl_partition16.md: 7.03 GB read +
+# 6.52 GB written for 1.452e8 propagations), per propagation, valid only for
 # the kernel sources it was taken on (sha256 prefix of solver.cu + learn.cuh +
 # cdcl.cuh); scaled to each launch by the propagations it processes.
-PROFILED_SOURCES = "06fb903fc3309244"
-DRAM_BYTES_PER_PROPAGATION = {"cdcl": (6.69e9 + 5.27e9) / 1.4798e8}
+PROFILED_SOURCES = "bae5e1b706dea040"
+DRAM_BYTES_PER_PROPAGATION = {"cdcl": (7.03e9 + 6.52e9) / 1.4520e8}
 
 
 def _kernel_sources_sha() -> str:
