@@ -46,7 +46,7 @@ WORKLOAD = "partition queries, 16-bit inputs (4,096 per GPU)"
 # 6.52 GB written for 1.452e8 propagations), per propagation, valid only for
 # the kernel sources it was taken on (sha256 prefix of solver.cu + learn.cuh +
 # cdcl.cuh); scaled to each launch by the propagations it processes.
-PROFILED_SOURCES = "bae5e1b706dea040"
+PROFILED_SOURCES = "c5803d532c6b4e9e"
 DRAM_BYTES_PER_PROPAGATION = {"cdcl": (7.03e9 + 6.52e9) / 1.4520e8}
 
 

@@ -34,15 +34,18 @@
 //  * Conflict analysis resolves the falsified clause with the reasons of
 //    current-level literals, newest first on the trail, until one
 //    current-level literal (the first UIP) is left; the lanes take the
-//    literals of each clause and a warp-wide backward scan of the trail
-//    finds the next literal to resolve. Every variable met is bumped.
+//    literals of each clause, and the next literal to resolve is the newest
+//    of the waiting ones, kept with their trail positions in shared memory
+//    (a warp-wide backward scan of the trail if more than CAND wait). Every
+//    variable met is bumped.
 //  * Hard instances are shared cube-and-conquer style through the DPLL mode's
 //    job ring: a busy warp that sees idle warps gives away the negation of
 //    its first free decision, together with the assumptions above it, as a
 //    cube, and keeps that decision as one more assumption itself (backjumps
 //    and restarts never undo assumptions). An instance is UNSAT once every
-//    cube is; a cube starts from its donor's activities with no learned
-//    clauses.
+//    cube is; a cube starts from its donor's activities and its short,
+//    low-LBD learned clauses. A unit of scuba_solve_units (an instance under
+//    the caller's assumptions) starts the same way, as a job with a prefix.
 //  * The search backjumps to the second-highest level of the learned clause
 //    and asserts its UIP literal there; decisions take the saved phase (the
 //    variable's last value, false at first); restarts follow the Luby

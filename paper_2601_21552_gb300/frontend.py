@@ -56,7 +56,6 @@ import numpy as np
 from workloads.ir import IR, OP
 
 AXES = ("x", "y", "z")
-BUILTINS = ("threadIdx", "blockIdx", "blockDim", "gridDim")
 
 
 class ProgramError(ValueError):
@@ -989,10 +988,8 @@ def analyze_incremental(texts: list, device: str = "cuda", bid_width: int = 16,
                                  if not k.startswith("@select")}
                 u += 1
         torch.cuda.synchronize()
-    reports, k = [], 0
-    for p, ks in zip(progs, kqs):
-        reports.append(Report([a for kq in ks for a in kq.accesses], use_after_free(p)))
-    return reports
+    return [Report([a for kq in ks for a in kq.accesses], use_after_free(p))
+            for p, ks in zip(progs, kqs)]
 
 
 def analyze(text: str, device: str = "cuda", bid_width: int = 16, **solve_opts) -> Report:

@@ -2,7 +2,6 @@
 two query families written as programs, decided through analyze_programs
 (one batch, through the C ABI), verdicts against the cited expectations and
 the closed forms, every witness satisfying its query."""
-import glob
 import os
 
 import pytest

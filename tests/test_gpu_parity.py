@@ -11,7 +11,6 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from closed_forms import partition_algebra
-from ir_eval import cnf_satisfied
 from workloads import queries
 from raw_cnf import model_ok as _model_ok, solve_raw as _solve_raw
 from workloads.ir import parse_text

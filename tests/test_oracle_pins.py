@@ -3,7 +3,6 @@ itself -- the definition (brute force over every input), closed forms derived
 from the constraint kinds of Sec. V-B, the paper's worked examples (Figs.
 1-5, Sec. VI-A), model re-verification, and an independent RUP checker."""
 import glob
-import itertools
 import os
 
 import numpy as np

@@ -5,7 +5,6 @@ the regular entry point, on two calls in a row (its scratch array keeps the
 previous call's contents), and refuse batches larger than its fixed scratch.
 
 Kept in its own file, named to be collected last."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
