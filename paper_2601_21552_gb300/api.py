@@ -203,17 +203,22 @@ def solve_units(db: DeviceBatch, unit_inst, asm_begin=None, asm_lits=None,
         for k, v in tuned.items():
             opts.setdefault(k, v)
     t = lambda a, dt: torch.as_tensor(np.asarray(a), dtype=dt).to(dev)
-    ui = t(unit_inst, torch.int32)
-    n_units = int(ui.numel())
+    ui_h = np.asarray(unit_inst, dtype=np.int64).reshape(-1)
+    n_units = len(ui_h)
+    ui = t(ui_h.astype(np.int32), torch.int32)
     ab = t(asm_begin, torch.int64) if asm_begin is not None else None
     al = t(asm_lits if asm_lits is not None and len(asm_lits) else [0], torch.int32) \
         if asm_begin is not None else None
-    nv = db.nv.to(torch.int64)[ui.long()] if n_units else torch.zeros(0, dtype=torch.int64,
-                                                                         device=dev)
-    mb = torch.zeros(max(n_units, 1), dtype=torch.int64, device=dev)
+    # model offsets on the host: an out-of-range instance index (the kernels
+    # report it and leave the unit UNKNOWN) takes no model space
+    nv_h = np.asarray(db.enc.inst_num_vars, dtype=np.int64)
+    ok = (ui_h >= 0) & (ui_h < db.n)
+    nvu = np.where(ok, nv_h[np.where(ok, ui_h, 0)] if db.n else 0, 0)
+    mb_h = np.zeros(max(n_units, 1), np.int64)
     if n_units:
-        mb[1:n_units] = torch.cumsum(nv, 0)[:-1]
-    total = int(nv.sum().item()) if n_units else 0
+        mb_h[1:n_units] = np.cumsum(nvu)[:-1]
+    mb = t(mb_h, torch.int64)
+    total = int(nvu.sum()) if n_units else 0
     verdict = torch.empty(max(n_units, 1), dtype=torch.uint8, device=dev)
     model = torch.zeros(max(total, 1), dtype=torch.uint8, device=dev) if want_model else None
     opts.setdefault("num_inputs", db.num_inputs)
