@@ -59,6 +59,33 @@ def _kernel_sources_sha() -> str:
     return h.hexdigest()[:16]
 
 
+# L2 traffic of the same kernel from one single-pass ncu capture of a full
+# launch (lts__t_bytes.sum: 135.57 GB for 1.445e8 propagations;
+# profiles/k_solve_cdcl_partition16.md), per propagation, under the same
+# source hash (idle warps polling the job ring included).
+L2_BYTES_PER_PROPAGATION = {"cdcl": 135.57e9 / 1.445e8}
+
+
+def l2_probe(dev, mib: int = 32, iters: int = 200) -> float:
+    """Achievable L2 bandwidth (GB/s, read + write) of a plain elementwise
+    copy whose source and destination (2 x `mib` MiB) stay resident in the
+    129 MB L2, timed with CUDA events after a warm-up."""
+    import torch
+    n = mib * (1 << 20) // 4
+    x = torch.ones(n, dtype=torch.float32, device=dev)
+    y = torch.empty_like(x)
+    for _ in range(10):
+        y.copy_(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(iters):
+        y.copy_(x)
+    e1.record()
+    e1.synchronize()
+    return 2.0 * n * 4 * iters / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
@@ -290,6 +317,20 @@ def _timed_arm(api, B, db, dev, stream, count, heur_opts, args, use_graph=True):
             "verdict": verdict.cpu().numpy().copy()}
 
 
+def _l2_line(arm, head, ws, dev):
+    """The search kernel's L2 throughput (ncu L2 bytes per propagation times
+    the measured propagations/s) against the achievable L2 bandwidth of
+    l2_probe: the survey's BCP-vs-L2 target."""
+    probe = l2_probe(dev)
+    per = L2_BYTES_PER_PROPAGATION.get(arm)
+    ok = per is not None and _kernel_sources_sha() == PROFILED_SOURCES
+    achieved = per * head["propagations_per_s"] / ws / 1e9 if ok else None
+    return {"achieved": achieved, "achievable": probe, "unit": "GB/s",
+            "frac": achieved / probe if achieved is not None else None,
+            "source": "ncu lts__t_bytes.sum per propagation (single pass, full launch) x "
+                      "propagations/s; achievable = L2-resident copy probe"}
+
+
 def run_ours(args):
     import torch
     ws, rank = _dist()
@@ -416,6 +457,7 @@ def run_ours(args):
         "e2e": {"value": count / float(np.median(e2e_t)), "unit": "verdicts/s",
                 "h2d_bytes_per_step": db.h2d_bytes, "d2h_bytes_per_step": count},
         "gpu_launches": 10 * args.steps,
+        "l2": _l2_line(arms[0], head, ws, dev),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": (DRAM_BYTES_PER_PROPAGATION[arms[0]] * head["propagations_per_s"]
