@@ -295,8 +295,9 @@ int scuba_abi_sizes(int64_t* out);
 /*
  * Serialized query IR (int64 array, layout documented in workloads/ir.py):
  * expression-tree nodes of Sec. V-A (FREE input words, constants, +, *, /k,
- * %k) and Boolean nodes (<, <=, ==, or, and, not), plus the asserted roots
- * (the kind 1/2/3 constraints of Sec. V-B).
+ * %k, and for C's unsigned k-bit wrap-around the low k bits and their
+ * complement) and Boolean nodes (<, <=, ==, or, and, not), plus the asserted
+ * roots (the kind 1/2/3 constraints of Sec. V-B).
  */
 typedef struct scuba_encoded scuba_encoded; /* opaque host handle */
 

@@ -15,8 +15,10 @@
  *   1. ir_*      : parse the serialized query IR (format in workloads/ir.py).
  *   2. enc_*     : bit-blast the IR to CNF with plain Tseitin gates (AND/XOR/OR
  *                  with full equivalences), ripple-carry adders, shift-and-add
- *                  multipliers, LSB-to-MSB comparator chains and division by a
- *                  constant through q,r with x = k*q + r, r < k.
+ *                  multipliers, LSB-to-MSB comparator chains, division by a
+ *                  constant through q,r with x = k*q + r, r < k, and C's
+ *                  unsigned k-bit wrap-around as bit selection (truncation)
+ *                  and negated bits (complement).
  *   3. dpll_*    : complete DPLL -- occurrence-list unit propagation to a
  *                  fixpoint, decide the unassigned variable of highest
  *                  activity (ties: lowest id), false polarity first, on
@@ -43,7 +45,8 @@
 
 enum {
   OP_FREE = 1, OP_CONST = 2, OP_ADD = 3, OP_MUL = 4, OP_ULT = 5, OP_ULE = 6,
-  OP_EQ = 7, OP_OR = 8, OP_AND = 9, OP_NOT = 10, OP_UDIV = 11, OP_UREM = 12
+  OP_EQ = 7, OP_OR = 8, OP_AND = 9, OP_NOT = 10, OP_UDIV = 11, OP_UREM = 12,
+  OP_TRUNC = 13, OP_NOTW = 14 /* y: a bit count, not a node */
 };
 
 enum { V_UNSAT = 0, V_SAT = 1, V_UNKNOWN = 2, V_ERROR = 3 };
@@ -71,6 +74,8 @@ static int ir_open(const int64_t *a, int64_t len, ir_t *ir) {
       if (x < 1 || x > 64) return -1;
     } else if (op == OP_CONST) {
       if (x < 0) return -1;
+    } else if (op == OP_TRUNC || op == OP_NOTW) {
+      if (x < 0 || x >= i || y < 1 || y > 64) return -1;
     } else if (op >= OP_ADD && op <= OP_UREM) {
       if (x < 0 || x >= i) return -1;
       if (op != OP_NOT && (y < 0 || y >= i)) return -1;
@@ -305,6 +310,16 @@ ocnf_t *oracle_encode(const int64_t *a, int64_t len) {
       case OP_CONST: wd[i] = w_const((uint64_t)x); break;
       case OP_ADD: wd[i] = w_add(&e, &wd[x], &wd[y]); break;
       case OP_MUL: wd[i] = w_mul(&e, &wd[x], &wd[y]); break;
+      case OP_TRUNC: { /* C unsigned conversion to y bits: keep the low y bits */
+        int w = wd[x].w < y ? wd[x].w : (int)y;
+        wd[i] = w_new(w);
+        for (int k = 0; k < w; k++) wd[i].b[k] = wd[x].b[k];
+        break;
+      }
+      case OP_NOTW: /* bitwise complement of the low y bits (missing bits are 0) */
+        wd[i] = w_new((int)y);
+        for (int k = 0; k < y; k++) wd[i].b[k] = -w_bit(&wd[x], k);
+        break;
       case OP_UDIV:
       case OP_UREM: {
         /* look for an earlier division of the same operand by the same constant */
@@ -595,6 +610,12 @@ static int eval_ir(const ir_t *ir, const uint64_t *inputs, u128 *wv, uint8_t *bv
         break;
       case OP_UDIV: wv[i] = wv[x] / wv[y]; break;
       case OP_UREM: wv[i] = wv[x] % wv[y]; break;
+      case OP_TRUNC:
+      case OP_NOTW: {
+        u128 m = (((u128)1) << y) - 1; /* y <= 64 */
+        wv[i] = op == OP_TRUNC ? (wv[x] & m) : (m - (wv[x] & m));
+        break;
+      }
       case OP_ULT: bv[i] = wv[x] < wv[y]; break;
       case OP_ULE: bv[i] = wv[x] <= wv[y]; break;
       case OP_EQ: bv[i] = wv[x] == wv[y]; break;

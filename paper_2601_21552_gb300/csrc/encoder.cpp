@@ -18,6 +18,8 @@
 //   a == b (asserted)    two binary clauses per bit, no fresh variables
 //   a / k, a % k         q, r fresh with a = k*q + r and r < k; shifts/masks
 //                        when k is a power of two
+//   a mod 2^k, ~a        C's unsigned k-bit wrap-around: the low k bits, and
+//                        their negations; no clauses
 // Input words get the lowest variable ids, most significant bit first, so a
 // lowest-id tie break branches on inputs from the top bit down.
 #include <algorithm>
@@ -36,7 +38,8 @@ constexpr int64_t kMagic = 0x53435542LL;
 constexpr int64_t kVersion = 1;
 enum Op : int64_t {
   kFree = 1, kConst = 2, kAdd = 3, kMul = 4, kUlt = 5, kUle = 6, kEq = 7,
-  kOr = 8, kAnd = 9, kNot = 10, kUdiv = 11, kUrem = 12
+  kOr = 8, kAnd = 9, kNot = 10, kUdiv = 11, kUrem = 12,
+  kTrunc = 13, kNotw = 14  // second field: a bit count in [1, 64]
 };
 
 // Literals are DIMACS ints; TRUE/FALSE constants are the two sentinels.
@@ -332,6 +335,14 @@ struct Encoder {
       case kMul: word[i] = mul(B, word[x], word[y]); break;
       case kUdiv: word[i] = divide(x, (uint64_t)node[4 * y + 1]).first; break;
       case kUrem: word[i] = divide(x, (uint64_t)node[4 * y + 1]).second; break;
+      case kTrunc:
+        word[i].assign(word[x].begin(), word[x].begin() + std::min<size_t>(word[x].size(), y));
+        if (word[i].empty()) word[i].push_back(kFalse);
+        break;
+      case kNotw:
+        word[i].resize((size_t)y);
+        for (int64_t k = 0; k < y; k++) word[i][k] = -bit(word[x], (size_t)k);
+        break;
       case kUlt: boolean[i] = ult(B, word[x], word[y]); break;
       case kUle: boolean[i] = -ult(B, word[y], word[x]); break;
       case kEq: boolean[i] = eq(B, word[x], word[y]); break;
@@ -356,12 +367,15 @@ int validate(const int64_t* a, int64_t len) {
                    op == kUdiv || op == kUrem;
     auto is_word = [&](int64_t j) {
       int64_t o = node[4 * j];
-      return o == kFree || o == kConst || o == kAdd || o == kMul || o == kUdiv || o == kUrem;
+      return o == kFree || o == kConst || o == kAdd || o == kMul || o == kUdiv || o == kUrem ||
+             o == kTrunc || o == kNotw;
     };
     if (op == kFree) {
       if (x < 1 || x > 64) return -1;
     } else if (op == kConst) {
       if (x < 0) return -1;
+    } else if (op == kTrunc || op == kNotw) {
+      if (x < 0 || x >= i || !is_word(x) || y < 1 || y > 64) return -1;
     } else if (op >= kAdd && op <= kUrem) {
       if (x < 0 || x >= i) return -1;
       if (op != kNot && (y < 0 || y >= i)) return -1;
@@ -380,7 +394,8 @@ int validate(const int64_t* a, int64_t len) {
     int64_t id = a[4 + 4 * n + k];
     if (id < 0 || id >= n) return -1;
     int64_t o = node[4 * id];
-    if (o == kFree || o == kConst || o == kAdd || o == kMul || o == kUdiv || o == kUrem)
+    if (o == kFree || o == kConst || o == kAdd || o == kMul || o == kUdiv || o == kUrem ||
+        o == kTrunc || o == kNotw)
       return -1;
   }
   return 0;

@@ -90,6 +90,14 @@ void divmod(const Big& a, uint64_t k, Big& q, Big& r) {
   r = from_u64((uint64_t)rem);
 }
 
+// a mod 2^k (k <= 64): the low k bits
+Big low_bits(const Big& a, int64_t k) {
+  Big r(a.begin(), a.begin() + std::min<size_t>(a.size(), (size_t)(k + 31) / 32));
+  if (k % 32 && r.size() == (size_t)(k + 31) / 32) r.back() &= (1u << (k % 32)) - 1;
+  trim(r);
+  return r;
+}
+
 }  // namespace
 
 int verify_words(const int64_t* ir, int64_t len, const uint64_t* words, int64_t nwords) {
@@ -102,7 +110,10 @@ int verify_words(const int64_t* ir, int64_t len, const uint64_t* words, int64_t 
   int64_t fi = 0;
   for (int64_t i = 0; i < n; i++) {
     int64_t op = node[4 * i], x = node[4 * i + 1], y = node[4 * i + 2];
-    if (op != 1 && op != 2 && (x < 0 || x >= i || (op != 10 && (y < 0 || y >= i)))) return -1;
+    bool imm = op == 13 || op == 14;  // TRUNC / NOTW: y is a bit count
+    if (op != 1 && op != 2 && (x < 0 || x >= i || (op != 10 && !imm && (y < 0 || y >= i))))
+      return -1;
+    if (imm && (y < 1 || y > 64)) return -1;
     switch (op) {
       case 1: {  // FREE
         if (fi >= nwords || x < 1 || x > 64) return -1;
@@ -120,6 +131,15 @@ int verify_words(const int64_t* ir, int64_t len, const uint64_t* words, int64_t 
         Big q, rem;
         divmod(w[x], (uint64_t)node[4 * y + 1], q, rem);
         w[i] = op == 11 ? q : rem;
+        break;
+      }
+      case 13: w[i] = low_bits(w[x], y); break;
+      case 14: {  // (2^y - 1) - (x mod 2^y), y <= 64
+        uint64_t m = y == 64 ? ~0ULL : (1ULL << y) - 1;
+        Big t = low_bits(w[x], y);
+        uint64_t v = t.empty() ? 0 : t[0];
+        if (t.size() > 1) v |= (uint64_t)t[1] << 32;
+        w[i] = from_u64(m - v);
         break;
       }
       case 5: b[i] = cmp(w[x], w[y]) < 0; break;

@@ -43,7 +43,11 @@ arguments by position):
 Expressions: integers, names, threadIdx/blockIdx/blockDim/gridDim .x/.y/.z,
 + - * / % (divisor a positive constant), parentheses; Booleans: < <= > >= ==
 != && || ! over expressions. Values are exact integers (no wrap-around);
-inputs are unsigned. ``#`` starts a comment; ``@key value`` after a statement
+inputs are unsigned. A program whose first statement is ``wrap W`` takes C's
+unsigned W-bit semantics instead: every value (inputs and constants too) is
+taken modulo 2^W, + - * wrap modulo 2^W, / and % divide the wrapped values;
+pointer arithmetic (partition offsets, the bounds check of an access) stays
+exact, as a 64-bit address computation does. ``#`` starts a comment; ``@key value`` after a statement
 (or on a line of its own) is metadata, e.g. ``access a[i] @expect SAT``.
 """
 from __future__ import annotations
@@ -81,6 +85,7 @@ class Program:
     host: list
     kernels: dict  # name -> Stmt(kind="kernel")
     meta: dict
+    wrap: int | None = None  # W of 'wrap W': unsigned W-bit arithmetic
 
 
 _TOKEN = re.compile(r"\s*(?:(\d+)|([A-Za-z_][A-Za-z_0-9]*(?:\.[xyz])?)|(<=|>=|==|!=|&&|\|\||[-+*/%()<>!,\[\]]))")
@@ -235,6 +240,7 @@ def parse(text: str) -> Program:
     host, kernels, meta = [], {}, {}
     stack = [("host", host, None)]  # (block kind, statement list, owning statement)
     last = None
+    wrap = None
     for n, raw in enumerate(text.splitlines(), 1):
         line_text = raw.split("#", 1)[0].strip()
         if not line_text:
@@ -267,6 +273,13 @@ def parse(text: str) -> Program:
             kernels[mk.group(1)] = st
             stack.append(("kernel", st.body, st))
             last = st
+            continue
+        if head == "wrap":
+            if host or kernels or wrap is not None or not rest.strip().isdigit():
+                raise ProgramError(f"line {n}: 'wrap W' must be the first statement")
+            wrap = int(rest)
+            if not 1 <= wrap <= 62:
+                raise ProgramError(f"line {n}: wrap width in [1, 62]")
             continue
         if head == "input" or head == "unknown":
             name, width = rest.split()
@@ -341,7 +354,7 @@ def parse(text: str) -> Program:
         last = st
     if len(stack) != 1:
         raise ProgramError("unterminated block (missing 'end')")
-    return Program(host, kernels, meta)
+    return Program(host, kernels, meta, wrap)
 
 
 # ---------------------------------------------------------------------------
@@ -360,11 +373,45 @@ class _Builder:
     """Builds one query. A word value is a pair (p, n) meaning p - n, each an
     IR node (_N) or a Python int (a folded constant); inputs are non-negative,
     so subtraction needs no wrap-around: comparisons move terms across.
-    Booleans are _N nodes or folded Python bools."""
+    Booleans are _N nodes or folded Python bools.
 
-    def __init__(self):
+    With wrap = W the program's own arithmetic (arith, constants, inputs) is
+    unsigned W-bit: every value it makes is a pair (v, 0) with v < 2^W, and a
+    result that may reach 2^W is truncated. The analysis' own arithmetic
+    (partition sizes, the bounds check) keeps using add/sub/less, exactly."""
+
+    def __init__(self, wrap: int | None = None):
         self.ir = IR()
         self.maxv = {}  # node id -> largest value it can take
+        self.wrap = wrap
+
+    def wrapv(self, v):
+        """v modulo 2^W (no node when v cannot reach 2^W)."""
+        if self.wrap is None:
+            return v
+        if not isinstance(v, _N):
+            return v % (1 << self.wrap)
+        if self.vmax(v) < (1 << self.wrap):
+            return v
+        r = _N(self.ir.trunc(v.i, self.wrap))
+        self.maxv[r.i] = (1 << self.wrap) - 1
+        return r
+
+    def arith(self, kind, x, y):
+        """The program's x + y, x - y or x * y."""
+        if self.wrap is None:
+            return {"+": self.add, "-": self.sub, "*": self.mul}[kind](x, y)
+        a, c = x[0], y[0]  # wrapped values: no negative part
+        if kind == "-":  # x - y = x + (2^W - y) = x + ~y + 1 (mod 2^W)
+            if isinstance(c, _N):
+                nc = _N(self.ir.notw(c.i, self.wrap))
+                self.maxv[nc.i] = (1 << self.wrap) - 1
+                r = self._bin("+", self._bin("+", a, nc), 1)
+            else:
+                r = self._bin("+", a, (-c) % (1 << self.wrap))
+        else:
+            r = self._bin(kind, a, c)
+        return (self.wrapv(r), 0)
 
     def node(self, v) -> int:
         return v.i if isinstance(v, _N) else self.ir.const(v)
@@ -396,7 +443,7 @@ class _Builder:
     def free(self, width, name):
         r = _N(self.ir.free(width, name))
         self.maxv[r.i] = (1 << width) - 1
-        return r
+        return self.wrapv(r)
 
     # word pairs
     def add(self, x, y):
@@ -489,7 +536,7 @@ class Access:
 def _eval(b: _Builder, env: dict, e, line):
     kind = e[0]
     if kind == "num":
-        return (e[1], 0)
+        return (b.wrapv(e[1]), 0)
     if kind == "name":
         if e[1] not in env:
             raise ProgramError(f"line {line}: unknown name {e[1]!r}")
@@ -503,7 +550,7 @@ def _eval(b: _Builder, env: dict, e, line):
             raise ProgramError(f"line {line}: divisor must be a positive constant")
         return b.divmod_(x, e[2][1], kind == "%", line)
     y = _eval(b, env, e[2], line)
-    return {"+": b.add, "-": b.sub, "*": b.mul}[kind](x, y)
+    return b.arith(kind, x, y)
 
 
 def _eval_bool(b: _Builder, env: dict, e, line):
@@ -618,7 +665,7 @@ def queries(prog: Program, bid_width: int = 16) -> list:
         if not any(st.kind == "launch" and st.args["kernel"] == kname for st in _flat(prog.host)):
             continue
         for idx, target in enumerate(accesses):
-            b = _Builder()
+            b = _Builder(prog.wrap)
             env, allocs, launch = _host_env(b, prog, kname, bid_width)
             kenv, sizes, shared = _kernel_env(b, env, allocs, launch, kern, bid_width)
             state = {"parts": {}, "found": False}
@@ -793,7 +840,7 @@ def kernel_queries(prog: Program, bid_width: int = 16) -> list:
     for kname, kern in prog.kernels.items():
         if kname not in launched:
             continue
-        b = _Builder()
+        b = _Builder(prog.wrap)
         env, allocs, launch = _host_env(b, prog, kname, bid_width)
         kenv, sizes, shared = _kernel_env(b, env, allocs, launch, kern, bid_width)
         found = []

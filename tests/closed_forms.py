@@ -90,3 +90,41 @@ def partition_algebra(w, k1, k0, a, c, k, j, guard) -> bool:
         f = lambda m: (a - k1 * k + k - 1) * m
         rhs = a - c + k0
     return f(1) >= rhs or f(M) >= rhs
+
+
+# -- the C wrap-around variant (unsigned W-bit arithmetic) -------------------
+# Brute force over every input: n, bdim, tid, bid each w-bit, kind 1
+# tid < bdim, and every program value reduced modulo 2^W as C's unsigned
+# W-bit arithmetic does; partition sizes and the bounds check are exact
+# (pointer arithmetic). Nothing here shares code with the encoders or the
+# front end.
+
+def _wrap_inputs(w):
+    import numpy as np
+    r = np.arange(1 << w, dtype=np.int64)
+    n, bdim, tid, bid = np.meshgrid(r, r, r, r, indexing="ij")
+    return n, bdim, tid, bid, tid < bdim
+
+
+def bounds_wrap(w, k1, k0, a, c, guard, W) -> bool:
+    M = 1 << W
+    n, bdim, tid, bid, ok = _wrap_inputs(w)
+    idx = (bid * bdim + tid) % M
+    off = (a * idx + c) % M
+    size = (k1 * n + k0) % M
+    if guard:
+        ok = ok & (idx < n)
+    return bool((ok & (off >= size)).any())
+
+
+def partition_wrap(w, k1, k0, a, c, k, j, guard, W) -> bool:
+    M = 1 << W
+    n, bdim, tid, bid, ok = _wrap_inputs(w)
+    m = n // k
+    start = (j * m) % M
+    end = ((j + 1) * m) % M if j < k - 1 else (k1 * n + k0) % M
+    idx = (bid * bdim + tid) % M
+    off = (a * idx + c) % M
+    if guard:
+        ok = ok & (idx < m)
+    return bool((ok & (off >= end - start)).any())

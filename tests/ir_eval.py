@@ -31,6 +31,10 @@ def evaluate(ir_array, inputs) -> bool:
             val[i] = val[x] // val[y]
         elif op == OP.UREM:
             val[i] = val[x] % val[y]
+        elif op == OP.TRUNC:
+            val[i] = val[x] % (1 << y)
+        elif op == OP.NOTW:
+            val[i] = (1 << y) - 1 - val[x] % (1 << y)
         elif op == OP.ULT:
             val[i] = int(val[x] < val[y])
         elif op == OP.ULE:

@@ -11,10 +11,11 @@ import numpy as np
 import pytest
 
 import oracle
-from closed_forms import bounds_algebra, partition_algebra
+from closed_forms import bounds_algebra, bounds_wrap, partition_algebra, partition_wrap
 from ir_eval import evaluate
 from paper_2601_21552_gb300 import frontend as F
 from workloads import queries
+from workloads.ir import OP
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PROGRAMS = sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "programs", "*.kp")))
@@ -166,6 +167,9 @@ end
     "end\n",                                         # stray end
     "input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  access q[0]\nend\n",
     "input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  local l[4]\n  access l[x / (x)]\nend\n",
+    "input n 8\nwrap 8\n",                         # wrap after another statement
+    "wrap 0\n",                                     # wrap width out of range
+    "wrap 63\n",
 ])
 def test_malformed_programs_are_rejected(bad):
     with pytest.raises(F.ProgramError):
@@ -233,3 +237,65 @@ def test_incremental_form_matches_per_access(path):
         one = sum(oracle.encode(kq.ir).nclauses for kq in F.kernel_queries(prog))
         each = sum(oracle.encode(a.ir).nclauses for a in per)
         assert one * 3 < each, (one, each)  # 10 accesses: 3,310 vs 12,732 clauses
+
+
+# ---------------------------------------------------------------------------
+# C wrap-around variant: unsigned W-bit program arithmetic
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w,d", [(4, 1), (4, 2), (5, 1), (5, 2)])
+def test_wrap_families_match_bruteforce(w, d):
+    """The bounds and partition families as programs under 'wrap W' (W = w + d,
+    inputs w-bit) against brute force over every input with explicit
+    modulo-2^W arithmetic."""
+    W = w + d
+    bp = [queries.config1_params(8400 + i, w=w) for i in range(24)]
+    pp = [queries.config2_params(8500 + i, w=w) for i in range(24)]
+    accs = [F.queries(F.parse(f"wrap {W}\n" + bounds_program(**p)), bid_width=w)[0] for p in bp]
+    accs += [F.queries(F.parse(f"wrap {W}\n" + partition_program(**p)), bid_width=w)[0]
+             for p in pp]
+    got, words = _solve(accs)
+    want = [int(bounds_wrap(**p, W=W)) for p in bp] + [int(partition_wrap(**p, W=W)) for p in pp]
+    assert got == want
+    assert set(want) == {0, 1}
+    exact = [int(bounds_algebra(**p)) for p in bp] + [int(partition_algebra(**p)) for p in pp]
+    if d == 1:
+        assert want != exact  # wrap-around changes verdicts of this sample
+    for a, v, wd in zip(accs, got, words):
+        if v == 1:
+            assert evaluate(a.ir, [int(x) for x in wd[:len(a.inputs)]])
+
+
+def test_wrap_program_against_exact_reading():
+    """The wrap-around golden program read with exact arithmetic (its 'wrap'
+    line removed) flips three of its four verdicts, as derived in its header."""
+    path = os.path.join(ROOT, "tests", "golden", "programs", "wrap_matrix8.kp")
+    text = open(path).read()
+    assert F.parse(text).wrap == 8
+    exact = F.parse(text.replace("wrap 8\n", ""))
+    assert exact.wrap is None
+    got, _ = _solve(F.queries(exact))
+    assert got == [0, 0, 1, 0]
+
+
+def test_wrap_truncates_only_what_can_wrap():
+    """Values that cannot reach 2^W get no truncation node; a product that
+    can gets one, and a subtraction of a node uses the W-bit complement."""
+    from workloads.ir import decode
+    text = """wrap 16
+input n 8
+input s 16
+malloc buf 300
+launch k grid(1) block(1) args(buf, n, s)
+kernel k(b, x, y)
+  access b[x + 3]
+  access b[y * 2]
+  access b[y - x]
+end
+"""
+    ops = [[nd[0] for nd in decode(a.ir)[0]] for a in F.queries(F.parse(text))]
+    assert OP.TRUNC not in ops[0] and OP.NOTW not in ops[0]
+    assert OP.TRUNC in ops[1] and OP.NOTW not in ops[1]
+    assert OP.TRUNC in ops[2] and OP.NOTW in ops[2]
+    got, _ = _solve(F.queries(F.parse(text)))
+    assert got == [0, 1, 1]  # 258 < 300; y*2 wraps to any even value; y - x wraps

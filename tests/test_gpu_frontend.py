@@ -8,7 +8,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from closed_forms import bounds_algebra, partition_algebra
+from closed_forms import bounds_algebra, bounds_wrap, partition_algebra, partition_wrap
 from ir_eval import evaluate
 from test_frontend import PROGRAMS, bounds_program, partition_program
 from workloads import queries
@@ -66,3 +66,37 @@ def test_incremental_form(frontend, search):
             assert (a.witness is not None) == (a.verdict == 1)
     flat = [a.verdict for r in inc for a in r.accesses]
     assert 0 in flat and 1 in flat
+
+
+@pytest.mark.parametrize("search", ["dpll", "cdcl"])
+def test_wrap_families_as_programs(frontend, search):
+    """The C wrap-around variant on the GPU: the two families under 'wrap W'
+    against brute force with explicit modulo-2^W arithmetic (5-bit inputs)
+    and against the oracle (8-bit inputs, W = 9 and 10)."""
+    import oracle
+    texts, want = [], []
+    for d in (1, 2):
+        for i in range(16):
+            p = queries.config1_params(8600 + i, w=5)
+            texts.append(f"wrap {5 + d}\n" + bounds_program(**p))
+            want.append(int(bounds_wrap(**p, W=5 + d)))
+            q = queries.config2_params(8700 + i, w=5)
+            texts.append(f"wrap {5 + d}\n" + partition_program(**q))
+            want.append(int(partition_wrap(**q, W=5 + d)))
+    reports = frontend.analyze_programs(texts, bid_width=5, search=search)
+    assert [r.accesses[0].verdict for r in reports] == want
+    assert set(want) == {0, 1}
+    t8 = []
+    for d in (1, 2):
+        t8 += [f"wrap {8 + d}\n" + bounds_program(**queries.config1_params(8800 + i, w=8))
+               for i in range(32)]
+        t8 += [f"wrap {8 + d}\n" + partition_program(**queries.config2_params(8900 + i, w=8))
+               for i in range(32)]
+    r8 = frontend.analyze_programs(t8, bid_width=8, search=search)
+    irs = [frontend.queries(frontend.parse(t), bid_width=8)[0].ir for t in t8]
+    ref = oracle.solve_queries(irs, max_words=16)["verdict"]
+    assert [r.accesses[0].verdict for r in r8] == [int(v) for v in ref]
+    for r in r8:
+        a = r.accesses[0]
+        if a.verdict == 1:
+            assert evaluate(a.ir, [a.witness[k] for k in a.inputs])

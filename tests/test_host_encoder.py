@@ -77,7 +77,8 @@ def _cnf_sat_under(nv, clauses, fixed):
 
 def _gadgets():
     out = []
-    for op in ("add", "mul", "div3", "rem5", "div4", "ult", "ule", "eq", "orcmp"):
+    for op in ("add", "mul", "div3", "rem5", "div4", "ult", "ule", "eq", "orcmp",
+               "wsub", "wmul", "wnot"):
         for t in range(0, 20, 3):
             ir = IR()
             x = ir.free(3)
@@ -98,6 +99,13 @@ def _gadgets():
                 ir.assert_(ir.not_(ir.ule(ir.mul(x, ir.const(t % 5 + 1)), y)))
             elif op == "eq":
                 ir.assert_(ir.or_(ir.eq(x, ir.const(t % 8)), ir.eq(ir.add(x, y), ir.const(t))))
+            elif op == "wsub":  # (x - y) mod 8 in C's unsigned 3-bit arithmetic
+                d = ir.trunc(ir.add(ir.add(x, ir.notw(y, 3)), ir.const(1)), 3)
+                ir.assert_(ir.eq(d, ir.const(t % 8)))
+            elif op == "wmul":
+                ir.assert_(ir.ult(ir.trunc(ir.mul(x, y), 4), ir.const(t % 16)))
+            elif op == "wnot":
+                ir.assert_(ir.ule(ir.notw(ir.add(x, y), 2), ir.trunc(y, 2)))
             else:
                 ir.assert_(ir.or_(ir.ult(x, y), ir.and_(ir.ule(y, x), ir.eq(y, ir.const(t % 8)))))
             out.append((op, t, ir))
@@ -178,3 +186,72 @@ def test_worked_examples_encode_to_3cnf(B):
     enc = B.scuba_encode_batch(irs)
     lens = np.diff(enc.clause_begin)
     assert lens.max() <= 3 and enc.n == len(files)
+
+
+def test_wrap_evaluator_against_modular_arithmetic():
+    """The test-side evaluator's truncation and complement against Python's
+    modular arithmetic (the other wrap pins compare with this evaluator)."""
+    for xv in range(8):
+        for yv in range(8):
+            ir = IR()
+            x, y = ir.free(3), ir.free(3)
+            d = ir.trunc(ir.add(ir.add(x, ir.notw(y, 3)), ir.const(1)), 3)
+            ir.assert_(ir.eq(d, ir.const((xv - yv) % 8)))
+            ir.assert_(ir.eq(ir.notw(ir.mul(x, y), 4), ir.const(15 - (xv * yv) % 16)))
+            assert evaluate(ir.to_array(), [xv, yv])
+
+
+def test_verify_wrap_ops_against_evaluator(B):
+    """The host re-verifier's truncation and complement (any bit count up to
+    64) against the test-side evaluator, on random models."""
+    rng = np.random.default_rng(11)
+    irs = []
+    for k in (1, 7, 31, 32, 33, 63, 64):
+        ir = IR()
+        x, y = ir.free(40), ir.free(40)
+        p = ir.mul(x, y)
+        ir.assert_(ir.ult(ir.trunc(p, k), ir.notw(ir.add(p, y), k)))
+        irs.append(ir.to_array())
+    enc = B.scuba_encode_batch(irs)
+    iib, widths, var = enc.inputs()
+    woff = np.concatenate([[0], np.cumsum(widths)])
+    for trial in range(4):
+        model = rng.integers(0, 2, size=enc.total_vars, dtype=np.uint8)
+        fails, ok = B.scuba_verify_batch(enc, np.ones(enc.n, np.uint8), model)
+        vb = enc.inst_var_begin
+        for i in range(enc.n):
+            words = []
+            for kk in range(iib[i], iib[i + 1]):
+                wv = 0
+                for j in range(widths[kk]):
+                    wv |= int(model[vb[i] + int(var[woff[kk] + j]) - 1]) << j
+                words.append(wv)
+            assert ok[i] == (1 if evaluate(irs[i], words) else 0), (i, trial)
+
+
+def test_wrap_queries_encode_equisatisfiably(B):
+    """Front-end queries under 'wrap W': the product encoder's CNFs, decided
+    by the oracle's CNF solver, give the verdicts the oracle reaches from its
+    own encoding of the same queries."""
+    import oracle
+    from paper_2601_21552_gb300 import frontend as F
+    from test_frontend import bounds_program, partition_program
+    texts = [open(os.path.join(ROOT, "tests", "golden", "programs", "wrap_matrix8.kp")).read()]
+    for d in (1, 2):
+        texts += [f"wrap {8 + d}\n" + bounds_program(**queries.config1_params(8800 + i, w=8))
+                  for i in range(16)]
+        texts += [f"wrap {8 + d}\n" + partition_program(**queries.config2_params(8900 + i, w=8))
+                  for i in range(16)]
+    irs = [a.ir for t in texts for a in F.queries(F.parse(t), bid_width=8)]
+    enc = B.scuba_encode_batch(irs)
+    cb, lits, icb = enc.clause_begin, enc.lits, enc.inst_clause_begin
+    cnfs = []
+    for i in range(enc.n):
+        c0, c1 = int(icb[i]), int(icb[i + 1])
+        l0 = int(cb[c0])
+        cnfs.append(oracle.CNF(int(enc.inst_num_vars[i]), cb[c0:c1 + 1] - l0,
+                               lits[l0:int(cb[c1])]))
+    got = oracle.solve_cnfs(cnfs)["verdict"]
+    want = oracle.solve_queries(irs, max_words=16)["verdict"]
+    assert got.tolist() == want.tolist()
+    assert set(want.tolist()) == {0, 1}

@@ -1,7 +1,8 @@
 """The oracle's pins have teeth: each test plants one plausible mistake in a
 text copy of oracle/oracle.c (a dropped carry, a flipped comparator, a
 missing partial product, a missing remainder bound, a DPLL that never flips
-a decision, a propagation that ignores units), builds that copy on the CPU,
+a decision, a propagation that ignores units, a truncation one bit short, a
+complement that leaves the high bits clear), builds that copy on the CPU,
 and checks that the pins -- brute force over every input and the closed
 forms -- reject it, while the unmodified source passes the same pins."""
 import ctypes
@@ -39,6 +40,12 @@ MUTANTS = {
     "propagation_ignores_units": (
         "if (nun == 1) {",
         "if (nun == 1 && 0) {"),
+    "truncation_drops_top_bit": (
+        "int w = wd[x].w < y ? wd[x].w : (int)y;",
+        "int w = wd[x].w < y ? wd[x].w : (int)y - 1;"),
+    "complement_misses_high_bits": (
+        "for (int k = 0; k < y; k++) wd[i].b[k] = -w_bit(&wd[x], k);",
+        "for (int k = 0; k < y; k++) wd[i].b[k] = k < wd[x].w ? -wd[x].b[k] : BF;"),
 }
 
 
@@ -105,6 +112,21 @@ def _pins_failed(L) -> int:
     for i, a in enumerate(gadget_irs):
         bf = L.oracle_brute_force(p(a), len(a), 12, p(wit))
         fails += int(bf != int(v[i]))
+    # C's unsigned wrap-around, input by input against Python's modular arithmetic
+    wrap_irs, want = [], []
+    for xv in range(8):
+        for yv in range(8):
+            ir = IR()
+            x, y = ir.free(3), ir.free(3)
+            d = ir.trunc(ir.add(ir.add(x, ir.notw(y, 3)), ir.const(1)), 3)
+            ir.assert_(ir.eq(x, ir.const(xv)))
+            ir.assert_(ir.eq(y, ir.const(yv)))
+            ir.assert_(ir.eq(d, ir.const((xv - yv) % 8)))
+            ir.assert_(ir.eq(ir.notw(x, 5), ir.const(31 - xv)))
+            wrap_irs.append(ir.to_array())
+            want.append(1)
+    v = _solve(L, wrap_irs)
+    fails += int(sum(int(a) != b for a, b in zip(v, want)))
     return fails
 
 

@@ -155,6 +155,40 @@ def test_gadgets_exhaustive(op):
                 assert evaluate(a, model_words(cnf, res["model"]))
 
 
+# C's unsigned k-bit arithmetic (the wrap-around variant), input by input
+# against Python's own modular arithmetic
+WRAP_GADGETS = {
+    # name: (IR builder on 3-bit x, y; the value it must take)
+    "sub3": (lambda ir, x, y: ir.trunc(ir.add(ir.add(x, ir.notw(y, 3)), ir.const(1)), 3),
+             lambda x, y: (x - y) % 8),
+    "mul3": (lambda ir, x, y: ir.trunc(ir.mul(x, y), 3), lambda x, y: (x * y) % 8),
+    "mul2_div3": (lambda ir, x, y: ir.udiv(ir.trunc(ir.mul(x, y), 2), 3),
+                  lambda x, y: ((x * y) % 4) // 3),
+    "notw5": (lambda ir, x, y: ir.add(ir.notw(x, 5), y), lambda x, y: (31 - x) + y),
+    "trunc8": (lambda ir, x, y: ir.trunc(ir.mul(x, y), 8), lambda x, y: x * y),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WRAP_GADGETS))
+def test_wrap_gadgets_per_input(name):
+    make, value = WRAP_GADGETS[name]
+    irs, want = [], []
+    for xv in range(8):
+        for yv in range(8):
+            for t in range(0, 40, 3):
+                ir = IR()
+                x, y = ir.free(3), ir.free(3)
+                r = make(ir, x, y)
+                ir.assert_(ir.eq(x, ir.const(xv)))
+                ir.assert_(ir.eq(y, ir.const(yv)))
+                ir.assert_(ir.eq(r, ir.const(t)))
+                irs.append(ir.to_array())
+                want.append(int(value(xv, yv) == t))
+    got = oracle.solve_queries(irs)["verdict"]
+    assert got.tolist() == want
+    assert [oracle.brute_force(a, max_bits=12)[0] for a in irs[::7]] == want[::7]
+
+
 # ---------------------------------------------------------------------------
 # Closed forms over the full config-1 family and the config-2 generator
 # ---------------------------------------------------------------------------

@@ -12,6 +12,11 @@ precision) and Boolean nodes, plus the list of Boolean roots that must all hold.
 Semantics (exact, non-wrapping): FREE nodes range over [0, 2^width); ADD and
 MUL are exact integer operations; UDIV/UREM divide by a positive constant
 (C floor division on non-negative values); ULT/ULE/EQ compare exactly.
+TRUNC and NOTW take an immediate bit count k instead of a second node: the
+low k bits of x, and their complement 2^k - 1 - (x mod 2^k). Together with
+ADD and MUL they express C's unsigned k-bit arithmetic, which wraps modulo
+2^k (x - y is TRUNC(x + NOTW(y) + 1)), for the wrap-around variant of the
+queries.
 
 Serialized layout (int64 array):
     [IR_MAGIC, IR_VERSION, N, R,  op_0, x_0, y_0, 0,  ...,  op_{N-1}, x, y, 0,
@@ -39,13 +44,16 @@ class OP:
     NOT = 10   # bool: y unused
     UDIV = 11  # word: x // y, y a CONST node with value >= 1
     UREM = 12  # word: x % y, y a CONST node with value >= 1
+    TRUNC = 13  # word: x mod 2^y, y = bit count (1..64), an immediate
+    NOTW = 14   # word: 2^y - 1 - (x mod 2^y), y = bit count (1..64), an immediate
 
-    WORD = {FREE, CONST, ADD, MUL, UDIV, UREM}
+    WORD = {FREE, CONST, ADD, MUL, UDIV, UREM, TRUNC, NOTW}
     BOOL = {ULT, ULE, EQ, OR, AND, NOT}
+    IMMEDIATE = {TRUNC, NOTW}
     NAMES = {
         "free": FREE, "const": CONST, "add": ADD, "mul": MUL, "ult": ULT,
         "ule": ULE, "eq": EQ, "or": OR, "and": AND, "not": NOT,
-        "udiv": UDIV, "urem": UREM,
+        "udiv": UDIV, "urem": UREM, "trunc": TRUNC, "notw": NOTW,
     }
 
 
@@ -84,6 +92,13 @@ class IR:
     # -- operators ------------------------------------------------------
     def _op(self, op: int, x: int, y: int = 0) -> int:
         n = len(self.nodes)
+        if op in OP.IMMEDIATE:
+            if not (0 <= x < n) or not self.is_word(x):
+                raise ValueError("operand must be an existing word node")
+            if not 1 <= y <= 64:
+                raise ValueError("bit count must be in [1, 64]")
+            self.nodes.append((op, x, y))
+            return n
         if not (0 <= x < n) or (op != OP.NOT and not (0 <= y < n)):
             raise ValueError("operand must be an existing node")
         kinds = [self.is_word(x)] + ([] if op == OP.NOT else [self.is_word(y)])
@@ -107,6 +122,12 @@ class IR:
 
     def urem(self, x, k: int):
         return self._op(OP.UREM, x, self.const(k))
+
+    def trunc(self, x, bits: int):
+        return self._op(OP.TRUNC, x, bits)
+
+    def notw(self, x, bits: int):
+        return self._op(OP.NOTW, x, bits)
 
     def ult(self, x, y):
         return self._op(OP.ULT, x, y)
@@ -175,7 +196,8 @@ def parse_text(text: str) -> tuple[IR, dict]:
     """Parse the small text form used by the golden fixtures.
 
     Lines: ``name = free W`` | ``name = const V`` | ``name = OP a b`` (a, b are
-    names or integer literals) | ``name = not a`` | ``assert name`` |
+    names or integer literals; for trunc/notw b is the bit count) |
+    ``name = not a`` | ``assert name`` |
     ``@key value`` (metadata). ``#`` starts a comment.
     """
     ir = IR()
@@ -212,6 +234,8 @@ def parse_text(text: str) -> tuple[IR, dict]:
         elif op in ("udiv", "urem"):
             k = int(toks[2])
             env[name] = ir.udiv(ref(toks[1]), k) if op == "udiv" else ir.urem(ref(toks[1]), k)
+        elif op in ("trunc", "notw"):  # the second operand is a bit count
+            env[name] = ir._op(OP.NAMES[op], ref(toks[1]), int(toks[2]))
         elif op in OP.NAMES:
             env[name] = ir._op(OP.NAMES[op], ref(toks[1]), ref(toks[2]))
         else:
