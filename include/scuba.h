@@ -177,6 +177,12 @@ typedef struct scuba_options {
                                 rounded up to 4), and as many 8-byte watch entries;
                                 0: default 2^18. At least max(max_vars + 8, 64),
                                 below 2^30 */
+  int32_t split_depth;       /* CDCL: a job shares a cube only while it is fewer than
+                                this many cube levels below its instance (its fixed
+                                levels beyond the unit's own assumptions); 0: no
+                                limit but the 248-literal prefix capacity. A cap
+                                bounds the cube tree, but a hard instance's deepest
+                                cubes then cannot share and run long */
 } scuba_options;
 
 /* Number of int64 counters per instance in scuba_options.stats. */

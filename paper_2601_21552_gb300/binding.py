@@ -50,7 +50,7 @@ class scuba_options(ctypes.Structure):
                 ("stats", _vp), ("order", _vp), ("abort_flag", _vp),
                 ("search_event_begin", _vp), ("search_event_end", _vp),
                 ("inst_num_inputs", _vp), ("trace", _vp), ("search", _i32),
-                ("restart_unit", _i32), ("learnt_words", _i64)]
+                ("restart_unit", _i32), ("learnt_words", _i64), ("split_depth", _i32)]
 
 
 class scuba_trace(ctypes.Structure):

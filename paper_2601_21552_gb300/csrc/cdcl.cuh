@@ -1007,6 +1007,11 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
     w.nd_fixed = w.nd;
   }
 
+  // fixed levels that are the unit's own assumptions, not cube literals
+  const uint32_t asm_levels =
+      S.unit_asm_begin ? (uint32_t)min(S.unit_asm_begin[unit + 1] - S.unit_asm_begin[unit],
+                                       (int64_t)MAX_PREFIX)
+                       : 0u;
   uint32_t iter = 0, conflicts = 0, since_restart = 0, restart_no = 1;
   uint32_t next_reduce = 2000u, reductions = 0;  // periodic database reduction
   uint32_t restart_at = (uint32_t)S.restart_unit * luby_cd(1);
@@ -1108,10 +1113,15 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
       return SCUBA_SAT;
     }
     // cube-and-conquer: hand the other side of the first free decision to an
-    // idle warp and keep this side as an assumption
+    // idle warp and keep this side as an assumption, up to split_depth cube
+    // levels below the instance. A cube relearns almost from scratch, so a
+    // job should share only once it has shown itself hard (split_min
+    // decisions): splitting easy jobs whenever warps are idle can cost an
+    // instance that needs a few hundred conflicts alone millions of them
     if (S.split && w.decisions >= (uint32_t)S.split_min &&
         (w.decisions % (uint32_t)S.split_interval) == 0 && w.nd > w.nd_fixed &&
-        w.nd_fixed + 1 <= (uint32_t)MAX_PREFIX) {
+        w.nd_fixed + 1 <= (uint32_t)MAX_PREFIX &&
+        w.nd_fixed < asm_levels + (uint32_t)S.split_depth) {
       uint32_t idle = 0;
       if (w.lane == 0) idle = *(volatile uint32_t*)&S.ctrl->idle;
       idle = __shfl_sync(FULL, idle, 0);
