@@ -42,12 +42,12 @@ WORKLOAD = "partition queries, 16-bit inputs (4,096 per GPU)"
 
 
 # DRAM traffic of the clause-learning search kernel from one single-pass ncu
-# capture of a full launch (profiles/k_solve_cdcl_partition16.md: 7.03 GB read +
-# 6.52 GB written for 1.452e8 propagations), per propagation, valid only for
+# capture of a full launch (profiles/k_solve_cdcl_partition16.md: 6.61 GB read +
+# 5.45 GB written for 1.4327e8 propagations), per propagation, valid only for
 # the kernel sources it was taken on (sha256 prefix of solver.cu + learn.cuh +
 # cdcl.cuh); scaled to each launch by the propagations it processes.
-PROFILED_SOURCES = "c5803d532c6b4e9e"
-DRAM_BYTES_PER_PROPAGATION = {"cdcl": (7.03e9 + 6.52e9) / 1.4520e8}
+PROFILED_SOURCES = "c77c54a6c17b6968"
+DRAM_BYTES_PER_PROPAGATION = {"cdcl": (6.61e9 + 5.45e9) / 1.4327e8}
 
 
 def _kernel_sources_sha() -> str:
@@ -60,10 +60,10 @@ def _kernel_sources_sha() -> str:
 
 
 # L2 traffic of the same kernel from one single-pass ncu capture of a full
-# launch (lts__t_bytes.sum: 135.57 GB for 1.445e8 propagations;
+# launch (lts__t_bytes.sum: 135.89 GB for 1.5016e8 propagations;
 # profiles/k_solve_cdcl_partition16.md), per propagation, under the same
 # source hash (idle warps polling the job ring included).
-L2_BYTES_PER_PROPAGATION = {"cdcl": 135.57e9 / 1.445e8}
+L2_BYTES_PER_PROPAGATION = {"cdcl": 135.89e9 / 1.5016e8}
 
 
 def l2_probe(dev, mib: int = 32, iters: int = 200) -> float:
@@ -215,9 +215,9 @@ def cpu_baseline(irs, target_s: float = 15.0, seed: int = 7, algo: str = "cdcl")
             "algo": algo,
             "sample": f"{done} of {len(irs)} queries drawn uniformly (seed {seed}), {t_used:.1f}s",
             "propagations_per_s": props / t_used,
-            "single_core": {"verdicts_per_s": done1 / t1 if t1 else None,
-                            "propagations_per_s": props1 / t1 if t1 else None,
-                            "sample": f"the first {done1} of that sample, {t1:.1f}s, 1 thread"}}
+            **({"single_core": {"verdicts_per_s": done1 / t1, "propagations_per_s": props1 / t1,
+                                "sample": f"the first {done1} of that sample, {t1:.1f}s, 1 thread"}}
+               if t1 else {})}
 
 
 def run_reference(args):
@@ -471,7 +471,7 @@ def run_ours(args):
                    "vars_total": enc.total_vars,
                    "l2": "inputs larger than L2 (CSR + occurrence lists > 1 GB)",
                    "encode_s": t_enc, "cuda_graph": args.graph, "parity": parity,
-                   "autotuned": tuned},
+                   "autotuned": {"dpll": tuned, "cdcl": tuned_cdcl}},
         "arms": summ,
         "e2e": {"value": count / float(np.median(e2e_t)), "unit": "verdicts/s",
                 "h2d_bytes_per_step": db.h2d_bytes, "d2h_bytes_per_step": count},
