@@ -1,0 +1,40 @@
+"""The benchmark's CPU-side pieces: the reference arm (the oracle timed on
+the host cores) prints one JSON line with the keys the bench contract asks
+for, and the CPU baseline reports its cores, sample and rates. No GPU."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert "workload" in d["config"]
+
+
+def test_cpu_baseline_fields():
+    sys.path.insert(0, ROOT)
+    import bench
+    irs, _ = bench._workload(0, 64, width=8)
+    c = bench.cpu_baseline(irs, target_s=0.5)
+    assert c["kind"] == "oracle" and c["algo"] == "cdcl" and c["cores"] >= 1
+    assert c["value"] > 0 and c["propagations_per_s"] > 0 and "sample" in c
+    assert c["single_core"]["verdicts_per_s"] > 0
+    d = bench.cpu_baseline(irs, target_s=0.5, algo="dpll")
+    assert d["algo"] == "dpll" and "single_core" not in d
