@@ -299,3 +299,35 @@ end
     assert OP.TRUNC in ops[2] and OP.NOTW in ops[2]
     got, _ = _solve(F.queries(F.parse(text)))
     assert got == [0, 1, 1]  # 258 < 300; y*2 wraps to any even value; y - x wraps
+
+
+def test_wrap_per_input_through_the_front_end():
+    """Pinned inputs: division after an overflowing product, subtraction that
+    underflows, and a guard computed in wrapped arithmetic, each against
+    Python's modular arithmetic (SAT iff the wrapped offset >= size)."""
+    cases = []
+    for n in (0, 3, 5, 64, 100, 200, 255):
+        for size in (1, 10, 40, 100):
+            cases.append((n, size, "(m * 4) / 3", ((n * 4) % 256) // 3, True))
+            cases.append((n, size, "m - 5", (n - 5) % 256, True))
+            # the guard wraps too: (m * 8) % 256 < 16 is the path condition
+            cases.append((n, size, "m + 7", (n + 7) % 256, (n * 8) % 256 < 16))
+    texts, want = [], []
+    for n, size, expr, off, guard_holds in cases:
+        body = f"access b[{expr}]"
+        if expr == "m + 7":
+            body = f"if m * 8 < 16\n    {body}\n  end"
+        texts.append(f"""wrap 8
+input n 8
+assert n == {n}
+malloc buf {size}
+launch k grid(1) block(1) args(buf, n)
+kernel k(b, m)
+  {body}
+end
+""")
+        want.append(int(guard_holds and off >= size))
+    accs = [F.queries(F.parse(t))[0] for t in texts]
+    got, _ = _solve(accs)
+    assert got == want
+    assert set(want) == {0, 1}
