@@ -310,7 +310,10 @@ typedef struct scuba_encoded scuba_encoded; /* opaque host handle */
 /*
  * Bit-blasts n queries on `nthreads` host threads (<= 0: all cores) into
  * 3-CNF. irs + ir_offsets[n+1] hold the serialized queries (host memory).
- * On success *out owns the encoded batch.
+ * On success *out owns the encoded batch. SCUBA_ERR_MALFORMED: a query is
+ * not valid IR; SCUBA_ERR_NOMEM: a query's circuit does not fit in host
+ * memory (products of wide words grow quadratically). On error nothing is
+ * allocated and scuba_last_error names the first failing query.
  */
 int scuba_encode_batch(int32_t n, const int64_t* irs, const int64_t* ir_offsets,
                        int32_t nthreads, scuba_encoded** out);
@@ -346,7 +349,8 @@ int scuba_encoded_release_clauses(scuba_encoded* enc);
  * map and evaluates the ORIGINAL integer constraints of the query exactly
  * (arbitrary precision). ok[i] = 1 verified, 0 model violates a constraint,
  * 2 not SAT (nothing to check). Returns the number of failures (>= 0) or a
- * negative status.
+ * negative status (SCUBA_ERR_ARG; SCUBA_ERR_NOMEM when an evaluation does
+ * not fit in host memory).
  */
 int scuba_verify_batch(const scuba_encoded* enc, const int64_t* irs, const int64_t* ir_offsets,
                        const uint8_t* verdict, const uint8_t* model, int32_t nthreads,

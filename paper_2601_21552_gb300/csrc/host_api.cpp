@@ -63,16 +63,39 @@ int scuba_encode_batch(int32_t n, const int64_t* irs, const int64_t* ir_offsets,
     scuba::set_error("scuba_encode_batch: bad arguments");
     return SCUBA_ERR_ARG;
   }
-  auto* enc = new scuba_encoded;
-  enc->cnf.resize(n);
-  std::atomic<int> bad{-1};
+  scuba_encoded* enc = nullptr;
+  try {
+    enc = new scuba_encoded;
+    enc->cnf.resize(n);
+  } catch (...) {
+    delete enc;
+    scuba::set_error("scuba_encode_batch: out of host memory");
+    return SCUBA_ERR_NOMEM;
+  }
+  // no exception may leave a pool thread (it would terminate the process):
+  // a query whose circuit does not fit in host memory is reported instead
+  std::atomic<int> bad{-1}, oom{-1};
   parallel_for(n, hw_threads(nthreads), [&](int i) {
     int64_t b = ir_offsets[i], e = ir_offsets[i + 1];
-    if (e < b || scuba::encode_query(irs + b, e - b, &enc->cnf[i]) != 0) {
+    int r;
+    try {
+      r = e < b ? -1 : scuba::encode_query(irs + b, e - b, &enc->cnf[i]);
+    } catch (...) {  // the batch is discarded below
+      int expect = -1;
+      oom.compare_exchange_strong(expect, i);
+      return;
+    }
+    if (r != 0) {
       int expect = -1;
       bad.compare_exchange_strong(expect, i);
     }
   });
+  if (oom.load() >= 0) {
+    scuba::set_error("scuba_encode_batch: out of host memory encoding query " +
+                     std::to_string(oom.load()));
+    delete enc;
+    return SCUBA_ERR_NOMEM;
+  }
   if (bad.load() >= 0) {
     scuba::set_error("scuba_encode_batch: malformed IR at query " + std::to_string(bad.load()));
     delete enc;
@@ -165,7 +188,8 @@ int scuba_verify_batch(const scuba_encoded* enc, const int64_t* irs, const int64
   std::vector<int64_t> vb(n + 1, 0);
   for (int i = 0; i < n; i++) vb[i + 1] = vb[i] + enc->cnf[i].nvars;
   std::atomic<int> fails{0};
-  parallel_for(n, hw_threads(nthreads), [&](int i) {
+  std::atomic<bool> oom{false};
+  auto check = [&](int i) {
     if (verdict[i] != SCUBA_SAT) {
       ok[i] = 2;
       return;
@@ -187,7 +211,19 @@ int scuba_verify_batch(const scuba_encoded* enc, const int64_t* irs, const int64
                                 words.data(), (int64_t)words.size());
     ok[i] = r == 1 ? 1 : 0;
     if (r != 1) fails.fetch_add(1);
+  };
+  parallel_for(n, hw_threads(nthreads), [&](int i) {
+    try {  // no exception may leave a pool thread
+      check(i);
+    } catch (...) {
+      ok[i] = 0;
+      oom.store(true);
+    }
   });
+  if (oom.load()) {
+    scuba::set_error("scuba_verify_batch: out of host memory");
+    return SCUBA_ERR_NOMEM;
+  }
   return fails.load();
 }
 
