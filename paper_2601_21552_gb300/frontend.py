@@ -41,8 +41,9 @@ arguments by position):
     assert BOOL                 device assert (holds from here on)
     access PTR[EXPR]            a load, store or atomic (the same to the analysis)
 Expressions: integers, names, threadIdx/blockIdx/blockDim/gridDim .x/.y/.z,
-+ - * / % (divisor a positive constant), parentheses; Booleans: < <= > >= ==
-!= && || ! over expressions. Values are exact integers (no wrap-around);
++ - * / % (divisor a positive constant), << and >> by a constant, & with a
+constant low-bits mask 2^k - 1 (x % 2^k; '&' binds tighter than comparisons,
+unlike C), parentheses; Booleans: < <= > >= == != && || ! over expressions. Values are exact integers (no wrap-around);
 inputs are unsigned. A program whose first statement is ``wrap W`` takes C's
 unsigned W-bit semantics instead: every value (inputs and constants too) is
 taken modulo 2^W, + - * wrap modulo 2^W, / and % divide the wrapped values;
@@ -88,7 +89,8 @@ class Program:
     wrap: int | None = None  # W of 'wrap W': unsigned W-bit arithmetic
 
 
-_TOKEN = re.compile(r"\s*(?:(\d+)|([A-Za-z_][A-Za-z_0-9]*(?:\.[xyz])?)|(<=|>=|==|!=|&&|\|\||[-+*/%()<>!,\[\]]))")
+_TOKEN = re.compile(r"\s*(?:(\d+)|([A-Za-z_][A-Za-z_0-9]*(?:\.[xyz])?)|"
+                    r"(<<|>>|<=|>=|==|!=|&&|\|\||[-+*/%()<>!,\[\]&]))")
 
 
 def _tokens(text: str, line: int) -> list:
@@ -162,6 +164,22 @@ class _Expr:
         raise ProgramError(f"line {self.line}: expected a comparison")
 
     def word(self):
+        # '&' binds tighter than the comparisons here (unlike C), looser
+        # than the shifts; shifts looser than + and -, as in C
+        a = self.shift()
+        while self.peek() == ("op", "&"):
+            self.take()
+            a = ("&", a, self.shift())
+        return a
+
+    def shift(self):
+        a = self.additive()
+        while self.peek() in (("op", "<<"), ("op", ">>")):
+            op = self.take()[1]
+            a = (op, a, self.additive())
+        return a
+
+    def additive(self):
         a = self.term()
         while self.peek() in (("op", "+"), ("op", "-")):
             op = self.take()[1]
@@ -544,11 +562,24 @@ def _eval(b: _Builder, env: dict, e, line):
         if not isinstance(v, tuple):
             raise ProgramError(f"line {line}: {e[1]!r} is not a value")
         return v
+    if kind == "&" and e[1][0] == "num" and e[2][0] != "num":
+        e = ("&", e[2], e[1])  # the mask on the right
     x, y = _eval(b, env, e[1], line), None
     if kind in ("/", "%"):
         if e[2][0] != "num" or e[2][1] < 1:
             raise ProgramError(f"line {line}: divisor must be a positive constant")
         return b.divmod_(x, e[2][1], kind == "%", line)
+    if kind in ("<<", ">>"):  # by a constant: * 2^k, or / 2^k
+        if e[2][0] != "num" or e[2][1] > 62:
+            raise ProgramError(f"line {line}: shift count must be a constant in [0, 62]")
+        if kind == ">>":
+            return b.divmod_(x, 1 << e[2][1], False, line)
+        return b.arith("*", x, (b.wrapv(1 << e[2][1]), 0))
+    if kind == "&":  # a low-bits mask 2^k - 1: % 2^k
+        m = e[2][1] if e[2][0] == "num" else -1
+        if m < 0 or (m + 1) & m:
+            raise ProgramError(f"line {line}: '&' takes a constant mask 2^k - 1")
+        return b.divmod_(x, m + 1, True, line)
     y = _eval(b, env, e[2], line)
     return b.arith(kind, x, y)
 

@@ -331,3 +331,67 @@ end
     got, _ = _solve(accs)
     assert got == want
     assert set(want) == {0, 1}
+
+
+def test_shifts_and_masks_per_input():
+    """<< and >> by constants and & with a 2^k - 1 mask, exact and under
+    'wrap 8', with pinned inputs, against Python's integer arithmetic."""
+    exprs = {
+        "(m << 3) >> 2": lambda n, M: ((n << 3) % M) >> 2,
+        "m & 31": lambda n, M: n & 31,
+        "(m << 4) & 255": lambda n, M: ((n << 4) % M) & 255,
+        "31 & (m + 40)": lambda n, M: ((n + 40) % M) & 31,
+        "m >> 3 << 1": lambda n, M: ((n >> 3) << 1) % M,
+    }
+    texts, want = [], []
+    for wrap in (None, 8):
+        M = (1 << 8) if wrap else (1 << 62)
+        for expr, f in exprs.items():
+            for n in (0, 7, 33, 100, 200, 255):
+                for size in (8, 40, 300):
+                    head = "wrap 8\n" if wrap else ""
+                    texts.append(f"""{head}input n 8
+assert n == {n}
+malloc buf {size}
+launch k grid(1) block(1) args(buf, n)
+kernel k(b, m)
+  access b[{expr}]
+end
+""")
+                    want.append(int(f(n, M) >= size % M))  # the size literal wraps too
+    got, _ = _solve([F.queries(F.parse(t))[0] for t in texts])
+    assert got == want
+    assert set(want) == {0, 1}
+
+
+def test_lane_and_warp_ids_program():
+    """Warp-level indexing (lane = tid & 31, warp = tid >> 5) into a shared
+    array of one element per thread: in bounds for any block size that is a
+    multiple of 32 up to 1024; a block of 33 threads with a 32-wide row per
+    warp reads past the end."""
+    def prog(bdim_expr, size_expr, guard=""):
+        body = "access s[(threadIdx.x >> 5) * 32 + (threadIdx.x & 31)]"
+        if guard:
+            body = f"if {guard}\n    {body}\n  end"
+        return f"""input w 5
+launch k grid(1) block({bdim_expr}) args(w)
+kernel k(q)
+  shared s[{size_expr}]
+  {body}
+end
+"""
+    texts = [prog("(w + 1) * 32", "(q + 1) * 32"),       # whole warps: in bounds
+             prog("(w + 1) * 32 + 1", "(q + 1) * 32"),   # one extra thread: OOB
+             prog("(w + 1) * 32 + 1", "(q + 1) * 32", "threadIdx.x < (q + 1) * 32")]
+    got, _ = _solve([F.queries(F.parse(t))[0] for t in texts])
+    assert got == [0, 1, 0]
+
+
+@pytest.mark.parametrize("bad", [
+    "input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  local l[4]\n  access l[x << x]\nend\n",
+    "input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  local l[4]\n  access l[x & 6]\nend\n",
+    "input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  local l[4]\n  access l[x >> 63]\nend\n",
+])
+def test_bad_shifts_and_masks_are_rejected(bad):
+    with pytest.raises(F.ProgramError):
+        F.queries(F.parse(bad))
