@@ -43,7 +43,8 @@ arguments by position):
 Expressions: integers, names, threadIdx/blockIdx/blockDim/gridDim .x/.y/.z,
 + - * / % (divisor a positive constant), << and >> by a constant, & with a
 constant low-bits mask 2^k - 1 (x % 2^k; '&' binds tighter than comparisons,
-unlike C), parentheses; Booleans: < <= > >= == != && || ! over expressions. Values are exact integers (no wrap-around);
+unlike C), min(a, b) and max(a, b) of non-negative values (a fresh value
+with its defining constraint), parentheses; Booleans: < <= > >= == != && || ! over expressions. Values are exact integers (no wrap-around);
 inputs are unsigned. A program whose first statement is ``wrap W`` takes C's
 unsigned W-bit semantics instead: every value (inputs and constants too) is
 taken modulo 2^W, + - * wrap modulo 2^W, / and % divide the wrapped values;
@@ -197,6 +198,13 @@ class _Expr:
         kind, val = self.take()
         if kind == "num":
             return ("num", val)
+        if kind == "name" and val in ("min", "max") and self.peek() == ("op", "("):
+            self.take("(")
+            a = self.word()
+            self.take(",")
+            c = self.word()
+            self.take(")")
+            return (val, a, c)
         if kind == "name":
             return ("name", val)
         if val == "(":
@@ -485,6 +493,26 @@ class _Builder:
         self.maxv[r.i] = min(self.vmax(x[0]), k - 1) if rem else self.vmax(x[0]) // k
         return (r, 0)
 
+    def minmax(self, kind, x, y, line):
+        """min(x, y) or max(x, y) as a fresh word r with its defining
+        equality (r = x and x <= y) or (r = y and y < x) (max: the other
+        way round) asserted: a kind 3 constraint of Sec. V-B."""
+        for v in (x, y):
+            if isinstance(v[1], _N) or v[1] != 0:
+                raise ProgramError(f"line {line}: {kind} needs non-negative operands "
+                                   "(no subtraction inside)")
+        a, c = x[0], y[0]
+        if not isinstance(a, _N) and not isinstance(c, _N):
+            return (min(a, c) if kind == "min" else max(a, c), 0)
+        hi = min(self.vmax(a), self.vmax(c)) if kind == "min" else max(self.vmax(a),
+                                                                           self.vmax(c))
+        r = (self.free(_bits(hi), f"{kind}@{line}"), 0)
+        self.maxv[r[0].i] = hi
+        first, second = (x, y) if kind == "min" else (y, x)
+        self.require(self.bor(self.band(self.equal(r, x), self.less(first, second, strict=False)),
+                              self.band(self.equal(r, y), self.less(second, first))))
+        return r
+
     def _cmp(self, fold, make, x, y):
         a = self._bin("+", x[0], y[1])
         b = self._bin("+", y[0], x[1])
@@ -562,6 +590,8 @@ def _eval(b: _Builder, env: dict, e, line):
         if not isinstance(v, tuple):
             raise ProgramError(f"line {line}: {e[1]!r} is not a value")
         return v
+    if kind in ("min", "max"):
+        return b.minmax(kind, _eval(b, env, e[1], line), _eval(b, env, e[2], line), line)
     if kind == "&" and e[1][0] == "num" and e[2][0] != "num":
         e = ("&", e[2], e[1])  # the mask on the right
     x, y = _eval(b, env, e[1], line), None

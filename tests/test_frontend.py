@@ -395,3 +395,56 @@ end
 def test_bad_shifts_and_masks_are_rejected(bad):
     with pytest.raises(F.ProgramError):
         F.queries(F.parse(bad))
+
+
+def test_min_max_per_input_and_clamp():
+    """min/max against Python's, with pinned inputs, exact and wrapped; a
+    clamped index is in bounds exactly when the clamp is below the size."""
+    exprs = {"min(m, 10)": lambda n: min(n, 10), "max(m, 50) - 40": lambda n: max(n, 50) - 40,
+             "min(m * 3, 200) + max(7, m & 7)": lambda n: min(n * 3, 200) + max(7, n & 7)}
+    texts, want = [], []
+    for expr, f in exprs.items():
+        for n in (0, 5, 33, 90, 255):
+            for size in (9, 60, 300):
+                texts.append(f"""input n 8
+assert n == {n}
+malloc buf {size}
+launch k grid(1) block(1) args(buf, n)
+kernel k(b, m)
+  access b[{expr}]
+end
+""")
+                want.append(int(f(n) >= size))
+    got, _ = _solve([F.queries(F.parse(t))[0] for t in texts])
+    assert got == want and set(want) == {0, 1}
+
+    def clamp(bound, wrap=""):
+        return f"""{wrap}input n 8
+input bd 8
+malloc buf 100
+launch k grid(?) block(bd) args(buf, n)
+kernel k(b, m)
+  let idx = blockIdx.x * blockDim.x + threadIdx.x
+  access b[min(idx, {bound})]
+  if max(idx, m) < 100
+    access b[idx]
+  end
+end
+"""
+    for wrap in ("", "wrap 16\n"):
+        got, words = _solve(F.queries(F.parse(clamp(99, wrap)), bid_width=8) +
+                            F.queries(F.parse(clamp(100, wrap)), bid_width=8))
+        assert got == [0, 0, 1, 0], wrap
+    # the incremental form agrees (the definitions are shared constraints)
+    prog = F.parse(clamp(100))
+    per, _ = _solve(F.queries(prog, bid_width=8))
+    forced = [force_selector(kq.ir, kq, k) for kq in F.kernel_queries(prog, bid_width=8)
+              for k in range(len(kq.selectors))]
+    assert [int(v) for v in oracle.solve_queries(forced)["verdict"]] == per
+
+
+def test_min_of_a_difference_is_rejected():
+    bad = ("input n 8\nlaunch k grid(1) block(1) args(n)\nkernel k(x)\n  local l[4]\n"
+           "  access l[min(x - 1, 3)]\nend\n")
+    with pytest.raises(F.ProgramError):
+        F.queries(F.parse(bad))
