@@ -1,0 +1,47 @@
+"""The autotuner's selection on the CPU, with a fake solve: the setting with
+the lowest MEAN time wins even when another has the lower median (the rare
+slow solves of the nondeterministic search are what the mean sees), failed
+solves count as infinite time and their statuses are recorded."""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def test_sweep_picks_lowest_mean(monkeypatch):
+    from paper_2601_21552_gb300 import api, autotune
+    # per setting: a sequence of (seconds, status) for successive solves
+    plan = {4: [(0.10, 0), (0.10, 0), (0.10, 0), (1.00, 0)],   # low median, a tail
+            48: [(0.14, 0), (0.15, 0), (0.14, 0), (0.15, 0)],  # steady
+            64: [(0.12, 0), (0.12, 0), (0.12, 0), (0.12, -4)]}  # one timeout
+    state = {"t": 0.0, "status": 0}
+    calls = {k: 0 for k in plan}
+
+    def fake_solve(db, want_model=False, stats=False, time_budget_ms=0, **opts):
+        k = opts["split_min"]
+        dt, st = plan[k][calls[k]]
+        calls[k] += 1
+        state["t"] += dt
+        state["status"] = st
+
+    monkeypatch.setattr(api, "solve", fake_solve)
+    monkeypatch.setattr(api, "status", lambda *a: state["status"])
+    monkeypatch.setattr(autotune.time, "perf_counter", lambda: state["t"])
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    best, trials = autotune.sweep(None, reps=4, space={"split_min": [4, 48, 64]},
+                                  fixed={"search": "cdcl"})
+    assert best["options"] == {"split_min": 48}
+    by = {t["options"]["split_min"]: t for t in trials}
+    assert by[4]["median_s"] < by[48]["median_s"] < by[4]["mean_s"]
+    assert by[64]["mean_s"] == float("inf") and by[64]["failed_status"] == [-4]
+    assert "failed_status" not in by[48]
+
+
+def test_load_sections(tmp_path):
+    from paper_2601_21552_gb300 import autotune
+    p = tmp_path / "t.json"
+    p.write_text('{"best": {"blocks_per_sm": 5}, "best_cdcl": {"split_min": 48}}')
+    assert autotune.load(str(p)) == {"blocks_per_sm": 5}
+    assert autotune.load(str(p), section="best_cdcl") == {"split_min": 48}
+    assert autotune.load(str(tmp_path / "missing.json")) == {}
+    # the committed file holds both sections
+    assert autotune.load(section="best_cdcl").get("split_min", 0) > 0
