@@ -215,7 +215,9 @@ int scuba_solve_batch_ex(const scuba_cnf_batch* batch, uint8_t* verdict, uint8_t
  * verdict[u] = SAT iff a model of the instance makes every assumption of u
  * true; UNSAT iff none does; UNKNOWN on a budget, time-out or error.
  *   - All arrays are DEVICE memory owned by the caller: unit_inst i32[n_units];
- *     asm_begin i64[n_units+1] (NULL: no assumptions), asm_lits i32;
+ *     asm_begin i64[n_units+1] (NULL: no assumptions), non-negative and
+ *     non-decreasing, asm_begin[n_units] no larger than the length of asm_lits i32
+ *     (the library does not know that length and cannot check it);
  *     unit_model_begin i64[n_units] (required when model != NULL: unit u's
  *     model goes to model[unit_model_begin[u] ..] for the num_vars of its
  *     instance; ranges must not overlap); verdict u8[n_units].

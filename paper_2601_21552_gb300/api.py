@@ -205,8 +205,18 @@ def solve_units(db: DeviceBatch, unit_inst, asm_begin=None, asm_lits=None,
         for k, v in tuned.items():
             opts.setdefault(k, v)
     t = lambda a, dt: torch.as_tensor(np.asarray(a), dtype=dt).to(dev)
-    ui_h = np.asarray(unit_inst, dtype=np.int64).reshape(-1)
+    host = lambda a: (a.cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a))
+    ui_h = host(unit_inst).astype(np.int64).reshape(-1)
     n_units = len(ui_h)
+    if asm_begin is not None:  # the offsets the kernels will follow into asm_lits
+        ab_h = host(asm_begin).astype(np.int64).reshape(-1)
+        n_lits = len(host(asm_lits).reshape(-1)) if asm_lits is not None else 0
+        if len(ab_h) != n_units + 1 or ab_h[0] < 0 or (np.diff(ab_h) < 0).any() \
+                or ab_h[-1] > n_lits:
+            raise ValueError("asm_begin must hold n_units + 1 non-negative, non-decreasing "
+                             "offsets into asm_lits")
+        asm_begin = ab_h
+        asm_lits = host(asm_lits) if asm_lits is not None else None
     ui = t(ui_h.astype(np.int32), torch.int32)
     ab = t(asm_begin, torch.int64) if asm_begin is not None else None
     al = t(asm_lits if asm_lits is not None and len(asm_lits) else [0], torch.int32) \

@@ -1,7 +1,9 @@
-"""The autotuner's selection on the CPU, with a fake solve: the setting with
-the lowest MEAN time wins even when another has the lower median (the rare
-slow solves of the nondeterministic search are what the mean sees), failed
-solves count as infinite time and their statuses are recorded."""
+"""Host-side logic on the CPU, no GPU calls. The autotuner's selection with a
+fake solve: the setting with the lowest MEAN time wins even when another has
+the lower median (the rare slow solves of the nondeterministic search are
+what the mean sees), failed solves count as infinite time and their statuses
+are recorded. The unit wrapper refuses assumption offsets that the kernels
+would follow past the end of the assumption literals."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -45,3 +47,23 @@ def test_load_sections(tmp_path):
     assert autotune.load(str(tmp_path / "missing.json")) == {}
     # the committed file holds both sections
     assert autotune.load(section="best_cdcl").get("split_min", 0) > 0
+
+
+@pytest.mark.parametrize("begin,lits", [
+    ([0, 1], [5, 6]),          # n_units + 1 offsets needed (3 units)
+    ([0, 2, 1, 2], [5, 6]),    # decreasing
+    ([0, 1, 2, 3], [5, 6]),    # past the end of asm_lits
+    ([-1, 0, 1, 2], [5, 6]),   # negative
+])
+def test_solve_units_rejects_bad_offsets_on_the_host(begin, lits):
+    """Offsets the kernels would follow past asm_lits are refused before any
+    device work (the library cannot know asm_lits' length)."""
+    import types
+
+    import numpy as np
+
+    from paper_2601_21552_gb300 import api
+    db = types.SimpleNamespace(icb=torch.zeros(1), n=1,
+                               enc=types.SimpleNamespace(inst_num_vars=np.array([3], np.int32)))
+    with pytest.raises(ValueError):
+        api.solve_units(db, [0, 0, 0], np.array(begin, np.int64), np.array(lits, np.int32))
