@@ -249,16 +249,23 @@ int scuba_solve_batch_host(const scuba_cnf_batch* batch, uint8_t* verdict, uint8
  * device global memory that the library declares statically; every GPU that
  * loads the library holds that array until the process exits. The call makes
  * no device allocation (no cudaMalloc/cudaFree, no allocating library call).
- *   - Arguments as for scuba_solve_batch_ex (device pointers); only
- *     SCUBA_HEUR_ACTIVITY; profiling outputs and search events are ignored.
+ *   - Arguments as for scuba_solve_batch_ex (device pointers). Supported:
+ *     the DPLL search (SCUBA_SEARCH_DPLL) with activity branching
+ *     (SCUBA_HEUR_ACTIVITY); other searches or heuristics give SCUBA_ERR_ARG.
+ *     Honoured options: decision_budget, time_budget_ms, split, split_min,
+ *     split_interval, split_depth, stats, order, abort_flag. Ignored: the
+ *     block shape (fixed below), trail_placement, profile, finish_ns,
+ *     search_event_begin/end, inst_num_inputs, trace.
  *   - Shape: one block of 4 warps per SM and a 256-job subtree ring, so a
  *     batch fits when its scratch (about 12*L + 8*(2*total_vars + n) + 12*C
  *     bytes plus 12*max_vars per warp) is at most 64 MiB; larger batches are
  *     rejected with SCUBA_ERR_TOO_LARGE and a message naming the limit.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
- *   - The call waits for `stream` and returns the device-side status itself.
+ *     (cudaGetSymbolAddress) with that device current.
+ *   - The call synchronises `stream` and reads the device-side status back
+ *     with a blocking copy before it returns that status (SCUBA_OK,
+ *     SCUBA_ERR_TIMEOUT, SCUBA_ERR_ABORTED, SCUBA_ERR_MALFORMED, ...), so it
+ *     cannot be recorded into a CUDA graph by stream capture.
  *   - All calls share the one array and it keeps the previous call's contents
  *     (everything that must start at zero is cleared by the call). Calls that
  *     overlap on the GPU -- on different streams, or from different host

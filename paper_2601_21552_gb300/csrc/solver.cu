@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -2048,6 +2049,7 @@ constexpr int kNoAllocWarpsPerBlock = 4;
 constexpr uint32_t kNoAllocRingCap = 256;
 constexpr int kMaxDevices = 256;
 void* g_noalloc_scratch_addr[kMaxDevices];  // device address of the array, per device
+std::mutex g_noalloc_mu;  // guards the per-device set-up and the shared attribute cache
 }  // namespace
 }  // namespace scuba
 
@@ -2090,11 +2092,14 @@ extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verd
   }
   // set-up, once per device, with that device current: the host-side name of
   // the array is not a device address, so ask the runtime for it
-  if (!g_noalloc_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail("cudaGetSymbolAddress", e);
-    g_noalloc_scratch_addr[dev] = p;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_scratch_addr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail("cudaGetSymbolAddress", e);
+      g_noalloc_scratch_addr[dev] = p;
+    }
   }
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -2223,9 +2228,19 @@ extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verd
   dev::k_init_ring<<<4, 256, 0, st>>>(sv.ring, ring_cap);
   dev::k_init_inst<<<(n + 255) / 256, 256, 0, st>>>(sv.pending, sv.done, sv.inst_dec, n);
   dev::k_start_clock<<<1, 1, 0, st>>>(sv.ctrl);
-  e = cudaFuncSetAttribute(dev::k_solve<dev::MODE_PLAIN>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
+  // the kernel attribute is shared with the regular entry points: only ever
+  // raise it, through the same per-device cache, so that a later regular
+  // call that needs more shared memory still finds its own grant in place
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    int& granted = scratch_map()[dev].smem_set[dev::MODE_PLAIN];
+    if ((int)smem > granted) {
+      e = cudaFuncSetAttribute(dev::k_solve<dev::MODE_PLAIN>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e);
+      granted = (int)smem;
+    }
+  }
   dev::k_solve<dev::MODE_PLAIN><<<sms, 32 * wpb, smem, st>>>(sv);
   dev::k_finalize<<<(n + 255) / 256, 256, 0, st>>>(sv);
   e = cudaGetLastError();
