@@ -9,6 +9,9 @@ tests/test_learned_ref.py.
 Model: z = X W1 + b1, h = relu(z), s = h w2 + b2 (16 -> 64 -> 1).
 Loss per node (a set of rows): cross-entropy between t / sum(t) and
 softmax(s) over the node's rows; the total is the sum over nodes.
+Training: Adam (Kingma and Ba, 2015, Algorithm 1) on the mean loss of each
+minibatch of nodes, restated by adam_step; pinned in tests/test_learned_ref.py
+by hand-derived values, scale invariance and convergence on a quadratic.
 """
 from __future__ import annotations
 
@@ -85,3 +88,15 @@ def grad(p: np.ndarray, X, nodes, target) -> np.ndarray:
     gW1 = X.T @ dh
     gb1 = dh.sum(axis=0)
     return flat(gW1, gb1, gw2, gb2)
+
+
+def adam_step(p: np.ndarray, m: np.ndarray, v: np.ndarray, g: np.ndarray, t: int,
+              lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam update (Kingma and Ba, 2015, Algorithm 1) in FP64: the biased
+    first and second moment estimates, their bias corrections at step t >= 1,
+    and the parameter step. Returns new (p, m, v); the inputs are unchanged."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return p - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

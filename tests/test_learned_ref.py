@@ -46,3 +46,41 @@ def test_loss_is_cross_entropy_of_softmax():
 def test_bf16_decode():
     u = np.array([0x3F80, 0xC000, 0x0000, 0x4049], np.uint16)
     assert R.bf16_to_f64(u).tolist() == [1.0, -2.0, 0.0, 3.140625]
+
+
+def test_adam_two_steps_hand_derived():
+    """Algorithm 1 of Kingma and Ba worked by hand for gradients 1 then 3
+    (beta1 0.9, beta2 0.999, eps 1e-8): step 1 moves by lr / (1 + eps) (m_hat = g, v_hat =
+    g^2); step 2 has m_hat = (0.09 + 0.3) / 0.19 and v_hat = (0.000999 +
+    0.009) / 0.001999, so it moves by lr * 2.052631... / sqrt(5.002001...)."""
+    lr = 0.01
+    p0, z = np.zeros(1), np.zeros(1)
+    p1, m1, v1 = R.adam_step(p0, z, z, np.array([1.0]), 1, lr)
+    assert abs(p1[0] - (-lr / (1.0 + 1e-8))) < 1e-15
+    assert abs(m1[0] - 0.1) < 1e-15 and abs(v1[0] - 0.001) < 1e-15
+    p2, m2, v2 = R.adam_step(p1, m1, v1, np.array([3.0]), 2, lr)
+    m_hat = (0.09 + 0.3) / 0.19
+    v_hat = (0.000999 + 0.009) / 0.001999
+    assert abs(m_hat - 2.0526315789473686) < 1e-12
+    assert abs(v_hat - 5.0020010005002) < 1e-9
+    assert abs((p1[0] - p2[0]) - lr * m_hat / (np.sqrt(v_hat) + 1e-8)) < 1e-14
+    assert abs((p1[0] - p2[0]) / lr - 0.917781) < 1e-6
+
+
+def test_adam_scale_invariance_and_convergence():
+    """Adam's step does not depend on the gradient's scale (eps aside), and it
+    takes a separable convex quadratic to its minimum."""
+    rng = np.random.default_rng(3)
+    gs = rng.normal(size=(5, 40))
+    pa = pb = np.zeros(40)
+    ma = va = mb = vb = np.zeros(40)
+    for t, g in enumerate(gs, start=1):
+        pa, ma, va = R.adam_step(pa, ma, va, g, t, 1e-2)
+        pb, mb, vb = R.adam_step(pb, mb, vb, 1000.0 * g, t, 1e-2)
+    assert np.allclose(pa, pb, rtol=1e-6, atol=1e-12)
+    a = rng.uniform(0.5, 5.0, size=40)
+    x_star = rng.normal(size=40)
+    x, m, v = np.zeros(40), np.zeros(40), np.zeros(40)
+    for t in range(1, 4001):
+        x, m, v = R.adam_step(x, m, v, a * (x - x_star), t, 1e-2)
+    assert np.abs(x - x_star).max() < 1e-2
