@@ -236,6 +236,62 @@ def test_config2_closed_form_w16_stored():
     assert (stored == want).all()
 
 
+def _read_stored(name):
+    head, digits = {}, []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line.startswith("#"):
+            if ":" in line:
+                k, v = line[1:].split(":", 1)
+                head[k.strip()] = v.strip()
+        elif line:
+            digits.append(line)
+    return head, np.frombuffer("".join(digits).encode(), dtype=np.uint8) - ord("0")
+
+
+def test_config1_and_config4_stored_verdicts_closed_form():
+    """The stored oracle verdicts of the 256 config-1 queries and of the 4,096
+    held-out config-4 queries (written by tests/golden/make_oracle_verdicts.py,
+    which calls only the oracle) agree with the closed forms, every query."""
+    _, v1 = _read_stored("config1_w8_oracle_verdicts.txt")
+    _, p1 = queries.config1(256)
+    assert (v1 == np.array([1 if bounds_algebra(**p) else 0 for p in p1])).all()
+    _, v4 = _read_stored("config4_test_oracle_verdicts.txt")
+    _, _, _, p4 = queries.config4_split(0, 4096)
+    assert len(v4) == 4096
+    assert (v4 == np.array([1 if partition_algebra(**p) else 0 for p in p4])).all()
+
+
+def test_config_caches_consistent_with_the_generators():
+    """The cached oracle verdicts of the large workloads (configs 3 and 5,
+    written by tests/golden/make_config_cache.py) belong to the instances the
+    generators produce now (fingerprint), hold one verdict per instance, and
+    agree with the closed form on config 5's bounds half wherever decided."""
+    import hashlib
+    for name in ("config3_oracle_verdicts.txt", "config5_oracle_verdicts.txt"):
+        if not os.path.exists(os.path.join(GOLDEN, name)):
+            pytest.skip(f"{name} not written yet")
+    head5, v5 = _read_stored("config5_oracle_verdicts.txt")
+    sat = queries.config5_sat(10000)
+    b_irs, b_params = queries.config5_bounds(10000)
+    h = hashlib.sha256()
+    for x in [l for _, l in sat] + list(b_irs):
+        h.update(np.ascontiguousarray(x, dtype=np.int64).tobytes())
+    assert head5["fingerprint"] == h.hexdigest()[:16]
+    assert len(v5) == 20000 == int(head5["count"])
+    cf = np.array([1 if bounds_algebra(**p) else 0 for p in b_params])
+    dec = v5[10000:] != 2
+    assert (v5[10000:][dec] == cf[dec]).all()
+    head3, v3 = _read_stored("config3_oracle_verdicts.txt")
+    irs, _ = queries.config3(65536)
+    h = hashlib.sha256()
+    for x in irs:
+        h.update(np.ascontiguousarray(x, dtype=np.int64).tobytes())
+    assert head3["fingerprint"] == h.hexdigest()[:16]
+    assert len(v3) == 65536 == int(head3["count"])
+    assert set(np.unique(v3).tolist()) <= {0, 1, 2}
+
+
 # ---------------------------------------------------------------------------
 # RUP checking of UNSAT refutations, and the checker itself
 # ---------------------------------------------------------------------------
