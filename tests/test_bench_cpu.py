@@ -31,10 +31,34 @@ def test_reference_arm_json_line():
 def test_cpu_baseline_fields():
     sys.path.insert(0, ROOT)
     import bench
-    irs, _ = bench._workload(0, 64, width=8)
+    irs, _ = bench._workload(64, width=8)
     c = bench.cpu_baseline(irs, target_s=0.5)
     assert c["kind"] == "oracle" and c["algo"] == "cdcl" and c["cores"] >= 1
     assert c["value"] > 0 and c["propagations_per_s"] > 0 and "sample" in c
     assert c["single_core"]["verdicts_per_s"] > 0
     d = bench.cpu_baseline(irs, target_s=0.5, algo="dpll")
     assert d["algo"] == "dpll" and "single_core" not in d
+
+
+def test_cpu_baseline_times_the_sample_in_one_pool_call(monkeypatch):
+    """The sample is solved by one call on every host thread (a chunked loop
+    would make each chunk wait for its slowest query and understate the
+    oracle), and the reported rate is that call's."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    calls = []
+    real = oracle.solve_queries
+
+    def spy(irs, threads=None, **kw):
+        calls.append((len(irs), threads))
+        return real(irs, threads=threads, **kw)
+
+    monkeypatch.setattr(oracle, "solve_queries", spy)
+    irs, _ = bench._workload(200, width=8)
+    c = bench.cpu_baseline(irs, target_s=0.2, algo="dpll")
+    threads = oracle.default_threads()
+    assert len(calls) == 2  # calibration, then the timed sample
+    assert all(t == threads for _, t in calls)
+    size = int(c["sample"].split()[0])
+    assert calls[1][0] == size and size >= calls[0][0]
