@@ -87,6 +87,152 @@ def test_forward_and_gradient_match_fp64(libs):
         assert np.abs(a - b).max() <= 1e-2 * scale + 1e-6, (name, np.abs(a - b).max(), scale)
 
 
+def test_adam_kernel_matches_fp64_restatement(libs):
+    """The training call's Adam steps (k_adam) against the FP64 restatement of
+    Kingma and Ba's Algorithm 1 on the same gradients: two minibatches of
+    three nodes, one epoch. The gradients are the GPU's own (pinned against
+    FP64 above); the second is taken at the weights after the first step."""
+    import ctypes
+    api, B = libs
+    tr, X, nodes, target = _synthetic_trace(api)
+    t = tr.struct()
+    s = torch.cuda.current_stream().cuda_stream
+    lr = 1e-2
+    net_a, net_b = api.Mlp(seed=7), api.Mlp(seed=7)
+    p0 = net_a.master.cpu().numpy().astype(np.float64)
+    w0 = net_a.weights.clone()
+    grad = torch.zeros(R.NPARAM + 2, dtype=torch.float32, device="cuda")
+    dS = torch.zeros(X.shape[0], dtype=torch.float32, device="cuda")
+
+    def gpu_grad(k0, k1, weights):
+        assert B._lib.scuba_mlp_grad(ctypes.byref(t), k0, k1, weights.data_ptr(),
+                                     grad.data_ptr(), dS.data_ptr(), s) == 0
+        g = grad.cpu().numpy().astype(np.float64)
+        return g[:R.NPARAM] / g[R.NPARAM + 1]   # mean over the nodes used
+
+    def train(net, n_nodes):
+        assert B._lib.scuba_mlp_train(ctypes.byref(t), n_nodes, net.master.data_ptr(),
+                                      net.m.data_ptr(), net.v.data_ptr(),
+                                      net.weights.data_ptr(), 1, 3, ctypes.c_float(lr),
+                                      None, s) == 0
+
+    # Where a gradient sits at rounding level its Adam step g / (|g| + eps)
+    # is ill-conditioned: the GPU sums gradients with atomics, so two calls
+    # differ in the last bits. b2's gradient is such a sum (dLoss/dscore adds
+    # up to zero over each node's rows); those entries are only held to
+    # Adam's step bound |step| <= lr (Kingma and Ba, Sec. 2.1).
+    g1 = gpu_grad(0, 3, w0)
+    train(net_b, 3)                                   # one step
+    p1_ref, m1_ref, v1_ref = R.adam_step(p0, 0 * p0, 0 * p0, g1, 1, lr)
+    p1 = net_b.master.cpu().numpy().astype(np.float64)
+    ok1 = np.abs(g1) >= 1e-3 * np.abs(g1).max()
+    ok1[R.NPARAM - 1] = False
+    assert ok1.sum() > 0.9 * R.NPARAM
+    assert np.abs((p1 - p0) - (p1_ref - p0))[ok1].max() <= 1e-6 + 1e-4 * lr
+    assert np.abs(p1 - p0).max() <= lr * (1 + 1e-5)
+    m1, v1 = net_b.m.cpu().numpy(), net_b.v.cpu().numpy()
+    assert np.allclose(m1[ok1], m1_ref[ok1], rtol=1e-5, atol=0)
+    assert np.allclose(v1[ok1], v1_ref[ok1], rtol=1e-5, atol=0)
+    g2 = gpu_grad(3, 6, net_b.weights)                # at the packed step-1 weights
+    train(net_a, 6)                                   # two steps in one call
+    p2_ref, m2_ref, v2_ref = R.adam_step(p1_ref, m1_ref, v1_ref, g2, 2, lr)
+    p2 = net_a.master.cpu().numpy().astype(np.float64)
+    ok2 = ok1 & (np.abs(g2) >= 1e-3 * np.abs(g2).max())
+    assert ok2.sum() > 0.8 * R.NPARAM
+    assert np.abs((p2 - p0) - (p2_ref - p0))[ok2].max() <= 1e-6 + 1e-3 * lr
+    assert np.abs(p2 - p0).max() <= 2 * lr * (1 + 1e-5)
+    m2, v2 = net_a.m.cpu().numpy(), net_a.v.cpu().numpy()
+    assert np.allclose(m2[ok2], m2_ref[ok2], rtol=1e-3, atol=0)
+    assert np.allclose(v2[ok2], v2_ref[ok2], rtol=1e-3, atol=0)
+    # the packed weights follow the master parameters (BF16 matrices, FP32 biases)
+    W1, b1, w2, b2 = R.unpack_weights(net_a.weights.cpu().numpy())
+    pm = net_a.master.cpu().numpy()
+    assert np.allclose(b1, pm[1024:1088]) and abs(b2 - pm[1152]) == 0.0
+    assert np.allclose(W1.reshape(-1), pm[:1024], rtol=2 ** -8, atol=1e-30)
+
+
+def test_root_features_match_cpu_restatement(libs):
+    """The 16 features the search records for every unassigned variable at
+    the root of each instance (after propagating its unit clauses), element
+    by element against a CPU restatement of their definitions (scuba.h):
+    per polarity, the clauses holding the literal that are not satisfied and
+    have 2 / 3 open literals, its occurrences, then activity (0 at the root),
+    the input-bit flag and position, depth 0, the assigned fraction, totals,
+    log2 of the occurrences, polarity balance and the constant 1."""
+    from test_gpu_bcp import cpu_closure
+    api, B = libs
+    irs, _ = queries.config2(48, w=10)
+    enc = B.scuba_encode_batch(irs)
+    db = api.DeviceBatch(enc, "cuda")
+    tr, _, _ = api.record_trace(db, depth=1, time_budget_ms=60000)
+    nodes, rows = tr.used()
+    assert nodes > 0
+    ninp = db.num_inputs.cpu().numpy()
+    n_inst = tr.node_inst.cpu().numpy()[:nodes]
+    n_row = tr.node_row.cpu().numpy()[:nodes]
+    n_nr = tr.node_nrows.cpu().numpy()[:nodes]
+    assert (tr.node_depth.cpu().numpy()[:nodes] == 0).all()
+    xg = tr.x.cpu().numpy().view(np.uint16)[:rows * 16].reshape(rows, 16)
+    varg = tr.var.cpu().numpy()[:rows]
+    checked = 0
+    for k in range(nodes):
+        i = int(n_inst[k])
+        cb = enc.clause_begin
+        cls = [enc.lits[cb[c]:cb[c + 1]].tolist()
+               for c in range(enc.inst_clause_begin[i], enc.inst_clause_begin[i + 1])]
+        nv = int(enc.inst_num_vars[i])
+        # the device drops repeated literals and tautologies; units only
+        # seed the propagation (they sit on no occurrence list)
+        norm = []
+        for c in cls:
+            c = list(dict.fromkeys(c))
+            if any(-x in c for x in c):
+                continue
+            norm.append(c)
+        conflict, val = cpu_closure(nv, norm, [])
+        assert not conflict
+        lit_val = lambda x: 0 if val[abs(x) - 1] == 0 else (
+            1 if (val[abs(x) - 1] == 1) == (x > 0) else -1)
+        occ = {}
+        for c in norm:
+            if len(c) >= 2:
+                for x in c:
+                    occ.setdefault(x, []).append([y for y in c if y != x])
+        unassigned = [v for v in range(nv) if val[v] == 0]
+        assert n_nr[k] == len(unassigned)
+        assert (varg[n_row[k]:n_row[k] + n_nr[k]] == unassigned).all()
+        assigned = nv - len(unassigned)
+        ni = int(ninp[i])
+        for r, v in enumerate(unassigned):
+            c2, c3, on = [0, 0], [0, 0], [0, 0]
+            for pol, x in enumerate((v + 1, -(v + 1))):
+                for others in occ.get(x, []):
+                    on[pol] += 1
+                    if len(others) > 2:
+                        continue          # long clauses are not counted
+                    vals = [lit_val(y) for y in others]
+                    if 1 in vals:
+                        continue
+                    open_ = 1 + vals.count(0)
+                    if open_ == 2:
+                        c2[pol] += 1
+                    elif open_ == 3:
+                        c3[pol] += 1
+            want = [c2[0] / 4, c3[0] / 4, c2[1] / 4, c3[1] / 4, on[0] / 8, on[1] / 8, 0.0,
+                    1.0 if v < ni else 0.0, v / ni if v < ni else 0.0, 0.0, assigned / nv,
+                    (c2[0] + c2[1]) / 8, (c3[0] + c3[1]) / 8, np.log2(1 + on[0] + on[1]) / 6,
+                    ((c2[0] + c3[0]) - (c2[1] + c3[1])) / 8, 1.0]
+            wb = _bf16_bits(np.array(want, np.float64))
+            got = xg[n_row[k] + r]
+            d = np.abs(got.astype(np.int64) - wb.astype(np.int64))
+            # counts are exact; a quotient or logarithm may land one BF16
+            # step away when its float32 value sits on a rounding boundary
+            assert (d[[0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 12, 14, 15]] == 0).all(), (k, v, got, wb)
+            assert (d[[8, 10, 13]] <= 1).all(), (k, v, got, wb)
+            checked += 1
+    assert checked > 1000
+
+
 def test_trace_records_closed_nodes(libs):
     api, B = libs
     irs, _ = queries.config2(64, w=10)
