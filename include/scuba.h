@@ -183,6 +183,13 @@ typedef struct scuba_options {
                                 limit but the 248-literal prefix capacity. A cap
                                 bounds the cube tree, but a hard instance's deepest
                                 cubes then cannot share and run long */
+  int32_t share_lbd;         /* CDCL: jobs that run beside other jobs of their instance
+                                (cubes, and the job that gave them away) publish
+                                their learned clauses of at most 12 literals and LBD
+                                <= share_lbd (units always) to a per-instance pool,
+                                and add the others' clauses at each restart; every
+                                learned clause is implied by the formula, so this
+                                never changes a verdict. 0: default 4; < 0: off */
 } scuba_options;
 
 /* Number of int64 counters per instance in scuba_options.stats. */

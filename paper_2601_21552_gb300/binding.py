@@ -14,7 +14,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libscuba.so")
+# SCUBA_LIBRARY=checked selects the checked build (device bounds checks that
+# report through the call's status); anything else the regular library
+LIB_PATH = os.path.join(_HERE, "_build", "libscuba_checked.so"
+                        if os.environ.get("SCUBA_LIBRARY") == "checked" else "libscuba.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libscuba.so not built ({LIB_PATH}); run __graft_entry__.build() "
@@ -50,7 +53,8 @@ class scuba_options(ctypes.Structure):
                 ("stats", _vp), ("order", _vp), ("abort_flag", _vp),
                 ("search_event_begin", _vp), ("search_event_end", _vp),
                 ("inst_num_inputs", _vp), ("trace", _vp), ("search", _i32),
-                ("restart_unit", _i32), ("learnt_words", _i64), ("split_depth", _i32)]
+                ("restart_unit", _i32), ("learnt_words", _i64), ("split_depth", _i32),
+                ("share_lbd", _i32)]
 
 
 class scuba_trace(ctypes.Structure):

@@ -3,6 +3,13 @@
 Host C++ translation units are compiled with g++, CUDA ones with nvcc
 (-gencode arch=compute_103a,code=sm_103a), all in parallel, then linked into
 paper_2601_21552_gb300/_build/libscuba.so. No cmake.
+
+The same sources are also linked, with the CUDA units compiled under
+-DSCUBA_CHECKED, into _build/libscuba_checked.so: the checked build, whose
+kernels test their indexes into the instance's buffers and report a failed
+check through the call's status (SCUBA_ERR_INTERNAL and a message naming the
+site) instead of touching memory out of bounds. The binding loads it when
+SCUBA_LIBRARY=checked is set.
 """
 from __future__ import annotations
 
@@ -17,6 +24,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libscuba.so")
+LIB_CHECKED = os.path.join(OUT, "libscuba_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 HOST_SRCS = ["encoder.cpp", "verify.cpp", "host_api.cpp"]
@@ -40,9 +48,11 @@ def _deps():
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _deps())
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+    if not force and all(os.path.exists(x) and os.path.getmtime(x) >= newest
+                         for x in (LIB, LIB_CHECKED)):
         return LIB
-    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(_nvcc()))), "include")
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", cuda_inc]
     defs = []
     for var in ("SCUBA_LEARNED_MINBLOCKS", "SCUBA_CDCL_MINBLOCKS"):
         if os.environ.get(var):
@@ -54,12 +64,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-c", os.path.join(CSRC, s),
                      "-o", o] + inc)
+    objs_checked = list(objs)
     for s in CUDA_SRCS:
-        o = os.path.join(OUT, s + ".o")
-        objs.append(o)
-        jobs.append([_nvcc(), "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-                     "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, s), "-o", o]
-                    + ARCH + inc + defs)
+        for checked in (False, True):
+            o = os.path.join(OUT, s + (".checked.o" if checked else ".o"))
+            (objs_checked if checked else objs).append(o)
+            jobs.append([_nvcc(), "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+                         "--expt-relaxed-constexpr", "-c", os.path.join(CSRC, s), "-o", o]
+                        + ARCH + inc + defs + (["-DSCUBA_CHECKED"] if checked else []))
 
     def run(cmd):
         if verbose:
@@ -73,9 +85,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    tmp = LIB + f".{os.getpid()}.tmp"
-    run([_nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-lpthread"])
-    os.replace(tmp, LIB)
+    for lib, o in ((LIB_CHECKED, objs_checked), (LIB, objs)):
+        tmp = lib + f".{os.getpid()}.tmp"
+        run([_nvcc(), "-shared", "-o", tmp] + o + ARCH + ["-lcudart", "-lpthread"])
+        os.replace(tmp, lib)
     return LIB
 
 

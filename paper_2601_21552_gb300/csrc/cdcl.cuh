@@ -132,7 +132,7 @@ __device__ __forceinline__ uint32_t lit_value_cd(const uint32_t* asg, uint32_t l
 // together. Returns false on a clash with the opposite value.
 __device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64_t why,
                                          uint32_t fresh = NB_FRESH) {
-  const uint32_t v = l >> 1, wi = v >> 3, sh = (v & 7u) * 4u;
+  const uint32_t v = WIDX(w, l >> 1, w.V, 11), wi = v >> 3, sh = (v & 7u) * 4u;
   const uint32_t val = (l & 1u) ? NB_F : NB_T;
   uint32_t old = w.asg[wi];
   for (;;) {
@@ -142,7 +142,7 @@ __device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64
     if (prev == old) break;
     old = prev;
   }
-  const uint32_t pos = atomicAdd(&w.ws->tail, 1u);
+  const uint32_t pos = WIDX(w, atomicAdd(&w.ws->tail, 1u), w.V, 12);
   w.trail[pos] = l;
   cd.ring[pos & (RING - 1u)] = make_uint2(l, pos);
   cd.pos[v] = pos;
@@ -186,11 +186,13 @@ __device__ void eval_long_cd(Warp& w, CdWarp& cd, uint32_t local) {
 // One occurrence entry of the falsified (old) literal f: (f | a) with b ==
 // NONE, (f | a | b), or a long clause. One claim site and one conflict site.
 __device__ __forceinline__ void eval_entry_cd(Warp& w, CdWarp& cd, uint32_t f, uint64_t e) {
-  const uint32_t a = (uint32_t)e, b = (uint32_t)(e >> 32);
-  if (a & LONG_CLAUSE) {
-    eval_long_cd(w, cd, a & ~LONG_CLAUSE);
+  const uint32_t a0 = (uint32_t)e, b0 = (uint32_t)(e >> 32);
+  if (a0 & LONG_CLAUSE) {
+    eval_long_cd(w, cd, a0 & ~LONG_CLAUSE);
     return;
   }
+  const uint32_t a = WIDX(w, a0, 2u * w.V, 13);
+  const uint32_t b = b0 == NONE ? NONE : WIDX(w, b0, 2u * w.V, 13);
   const uint32_t na = nib(w.asg, a >> 1);
   const uint32_t va = nib_value(na, a);
   uint32_t nb = 0, vb = LV_F;  // a binary entry has no third literal: read it as false
@@ -333,10 +335,10 @@ __device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f, ui
     bool pending = false;
     uint32_t at = 0, c = 0;
     if (e < total) {
-      at = jbeg + (e - jex);
+      at = WIDX(w, jbeg + (e - jex), cd.pool_cap, 16);
       const uint64_t ent = cd.pool[at];
-      c = (uint32_t)ent;
-      pending = lit_value_cd(w.asg, (uint32_t)(ent >> 32)) != LV_T;  // blocker
+      c = WIDX(w, (uint32_t)ent, cd.top, 17);
+      pending = lit_value_cd(w.asg, WIDX(w, (uint32_t)(ent >> 32), 2u * w.V, 18)) != LV_T;  // blocker
     }
     uint32_t g = NONE;
     uint64_t moved = 0;
@@ -415,7 +417,7 @@ __device__ __forceinline__ void static_batch(Warp& w, CdWarp& cd, uint32_t nlit,
     const uint32_t jbeg = __shfl_sync(FULL, beg, j);
     const uint32_t jex = __shfl_sync(FULL, excl, j);
     const uint32_t jf = __shfl_sync(FULL, f, j);
-    if (e < total) eval_entry_cd(w, cd, jf, __ldg(&w.ent[jbeg + (e - jex)]));
+    if (e < total) eval_entry_cd(w, cd, jf, __ldg(&w.ent[WIDX(w, jbeg + (e - jex), w.ent_end, 15)]));
   }
 }
 
@@ -439,7 +441,7 @@ __device__ bool bcp_cd(Warp& w, CdWarp& cd) {
         const uint32_t t = trail_at(w, cd, base + w.lane);
         const uint32_t v = t >> 1;
         atomicAnd(&w.asg[v >> 3], ~(NB_FRESH << ((v & 7u) * 4u)));  // no longer fresh
-        f = t ^ 1u;
+        f = WIDX(w, t ^ 1u, 2u * w.V, 14);
         beg = __ldg(&w.occ[f]);
         cnt = __ldg(&w.occ[f + 1]) - beg;
         if (cd.top) {
@@ -493,7 +495,7 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
       const uint32_t k = k0 + w.lane;
       uint32_t q = NONE;
       if (k < cnt) q = src ? src[k] : csr ? code_of(csr[k]) : (k == 0 ? r0 : k == 1 ? r1 : r2);
-      const uint32_t v = q >> 1;
+      const uint32_t v = q == NONE ? NONE >> 1 : WIDX(w, q >> 1, w.V, 21);
       bool take = false;
       uint32_t mk = 0, lv = 0, ps = 0;
       if (q != NONE && (p == NONE || v != (p >> 1))) {
@@ -523,7 +525,7 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
         }
       }
       const uint32_t lowm = __ballot_sync(FULL, take && lv < lvl);
-      if (take && lv < lvl) cd.learnt[n + __popc(lowm & ((1u << w.lane) - 1u))] = q;
+      if (take && lv < lvl) cd.learnt[WIDX(w, n + __popc(lowm & ((1u << w.lane) - 1u)), w.V, 20)] = q;
       n += __popc(lowm);
       __syncwarp();
     }
@@ -937,6 +939,142 @@ __device__ uint32_t pick_cd(Warp& w) {
   return best_v;
 }
 
+// ---- clauses shared between the jobs of one instance ----------------------
+//
+// Every learned clause is implied by the formula alone (assumption literals
+// enter it as decisions, level-0 literals are dropped only when false at
+// level 0), so any job of the same instance may use it, whatever its own
+// assumptions. Jobs that run beside others of their instance publish their
+// short, low-LBD learned clauses to a per-instance pool and read the others'
+// at each restart. A pool is a ring of fixed-size records in global memory:
+// a writer reserves record r with one atomicAdd on the pool's cursor, writes
+// the body, fences, then writes the header r + 1. A reader takes record r only
+// if its header reads r + 1 before the body and the cursor shows, after the
+// body, that no writer can have reserved the record's slot again (cursor <=
+// r + cap). Records that fail either check are skipped, never guessed.
+
+// Publish learnt[0..n) (1 <= n <= SHARE_MAXLEN) with its LBD (all lanes).
+__device__ void share_publish(const Solve& S, Warp& w, CdWarp& cd, uint32_t n, uint32_t lbd,
+                              int64_t slot) {
+  const uint32_t p = (uint32_t)w.inst & S.share_mask;
+  unsigned long long r = 0;
+  if (w.lane == 0) r = atomicAdd(&S.share_cur[p], 1ull);
+  r = __shfl_sync(FULL, r, 0);
+  uint32_t* rec =
+      S.share + ((size_t)p * S.share_cap + (uint32_t)(r & (S.share_cap - 1u))) * SHARE_REC;
+  if (w.lane >= 1 && w.lane < (int)SHARE_REC) {
+    uint32_t x;
+    if (w.lane == 1) x = (uint32_t)w.inst;
+    else if (w.lane == 2) x = n | (min(lbd, 255u) << 8);
+    else if (w.lane == 3) x = (uint32_t)slot;
+    else x = (uint32_t)(w.lane - 4) < n ? cd.learnt[w.lane - 4] : NONE;
+    *(volatile uint32_t*)&rec[w.lane] = x;
+  }
+  __threadfence();
+  __syncwarp();
+  if (w.lane == 0) *(volatile uint32_t*)&rec[0] = (uint32_t)(r + 1ull);
+  __syncwarp();
+}
+
+// Read the pool's records published since *rd by other jobs of this
+// instance, at most 256 per call, into the learned-clause database (all
+// lanes, at the bottom level after a restart). Each clause is watched on two
+// literals that are not false if it has them, else on its one such literal
+// and the false literal of highest level; a clause with one open literal
+// left implies it, one with none refutes the job. Returns false in that
+// case (the job's assumptions contradict the formula), true otherwise.
+__device__ bool share_import(const Solve& S, Warp& w, CdWarp& cd, int64_t slot,
+                             unsigned long long& rd) {
+  const uint32_t p = (uint32_t)w.inst & S.share_mask;
+  const unsigned long long cap = S.share_cap;
+  unsigned long long cur = 0;
+  if (w.lane == 0) cur = *(volatile unsigned long long*)&S.share_cur[p];
+  cur = __shfl_sync(FULL, cur, 0);
+  unsigned long long from = rd;
+  if (cur > cap / 2 && from < cur - cap / 2) from = cur - cap / 2;  // skip what may be overwritten
+  const unsigned long long to = min(cur, from + 256ull);
+  const uint64_t no_reason = ~0ull;
+  bool ok_all = true;
+  for (unsigned long long base = from; base < to && ok_all; base += 32) {
+    const unsigned long long r = base + (unsigned long long)w.lane;
+    bool ok = r < to;
+    uint32_t n = 0, lbd = 0, lit[SHARE_MAXLEN];
+    const uint32_t* rec = S.share + ((size_t)p * S.share_cap + (uint32_t)(r & (cap - 1u))) * SHARE_REC;
+    if (ok) ok = *(const volatile uint32_t*)&rec[0] == (uint32_t)(r + 1ull);
+    if (ok) {
+      __threadfence();
+      const uint32_t ins = *(const volatile uint32_t*)&rec[1];
+      const uint32_t nl = *(const volatile uint32_t*)&rec[2];
+      const uint32_t prod = *(const volatile uint32_t*)&rec[3];
+      n = nl & 255u;
+      lbd = nl >> 8;
+      ok = ins == (uint32_t)w.inst && prod != (uint32_t)slot && n >= 1 && n <= SHARE_MAXLEN;
+#pragma unroll
+      for (uint32_t k = 0; k < SHARE_MAXLEN; k++) {
+        lit[k] = *(const volatile uint32_t*)&rec[4 + k];
+        if (k < n && lit[k] >= 2u * w.V) ok = false;
+      }
+      __threadfence();
+      const unsigned long long now = *(volatile unsigned long long*)&S.share_cur[p];
+      if (now > r + cap) ok = false;  // the slot may hold a newer record by now
+    }
+    for (uint32_t todo = __ballot_sync(FULL, ok); todo && ok_all; todo &= todo - 1u) {
+      const int j = __ffs(todo) - 1;
+      const uint32_t nj = __shfl_sync(FULL, n, j), lbdj = __shfl_sync(FULL, lbd, j);
+      uint32_t my = NONE;
+#pragma unroll
+      for (uint32_t k = 0; k < SHARE_MAXLEN; k++) {
+        const uint32_t x = __shfl_sync(FULL, lit[k], j);
+        if ((uint32_t)w.lane == k) my = x;
+      }
+      const bool have = (uint32_t)w.lane < nj;
+      const uint32_t val = have ? lit_value_cd(w.asg, my) : LV_F;
+      const uint32_t lvl = have && val == LV_F ? cd.level[my >> 1] : 0u;
+      const uint32_t nf = __ballot_sync(FULL, have && val != LV_F);
+      if (nf == 0u) {  // every literal false: the job's assumptions are refuted
+        ok_all = false;
+        break;
+      }
+      const int w0 = __ffs(nf) - 1;
+      int w1 = -1;
+      if (__popc(nf) >= 2) {
+        w1 = __fns(nf, 0, 2);
+      } else if (nj >= 2) {  // the false literal of the highest level (lowest lane on ties)
+        const bool cand = have && w.lane != w0;
+        uint32_t best = cand ? lvl : 0u;
+        for (int d = 16; d > 0; d >>= 1) best = max(best, __shfl_xor_sync(FULL, best, d));
+        w1 = __ffs(__ballot_sync(FULL, cand && lvl == best)) - 1;
+      }
+      const bool unit = __popc(nf) == 1 && __shfl_sync(FULL, val, w0) == LV_U;
+      const uint32_t first = __shfl_sync(FULL, my, w0);
+      if (nj == 1) {  // a unit clause: its literal holds in every model
+        if (unit && w.lane == 0) imply_cd(w, cd, first, no_reason, 0u);
+        __syncwarp();
+        continue;
+      }
+      if ((uint64_t)cd.top + clause_words(nj) > cd.arena_words || cd.full) break;
+      // the two watches first, then the rest in record order
+      const uint32_t rest = __ballot_sync(FULL, have) & ~(1u << w0) & ~(1u << w1);
+      if (have) {
+        uint32_t at;
+        if (w.lane == w0) at = 0;
+        else if (w.lane == w1) at = 1;
+        else at = 2u + __popc(rest & ((1u << w.lane) - 1u));
+        cd.learnt[at] = my;
+      }
+      __syncwarp();
+      const uint32_t c = add_learnt(w, cd, nj, lbdj);
+      if (unit) {
+        if (w.lane == 0) imply_cd(w, cd, cd.learnt[0], (uint64_t)(LEARNT_REF | c), 0u);
+        __syncwarp();
+      }
+    }
+  }
+  rd = to;
+  __syncwarp();
+  return ok_all;
+}
+
 // One job: an instance, or a cube of it (the job's literals as assumptions,
 // from the subtree-sharing ring), start to verdict. Returns SAT, UNSAT (for a
 // cube: no model extends it) or UNKNOWN.
@@ -967,6 +1105,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
   w.occ = S.occ_begin + S.occ_base[inst];
   const int64_t lbase = S.icb[inst] < S.icb[inst + 1] ? S.cb[S.icb[inst]] : 0;
   w.ent = S.ent + lbase;
+  warp_checks(w, S.ctrl);
   w.head = 0;
   w.nd = 0;
   w.nd_fixed = 0;
@@ -999,7 +1138,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
       const uint32_t val = lit_value_cd(w.asg, l);
       if (val == LV_F) return SCUBA_UNSAT;
       if (val == LV_T) continue;
-      if (w.lane == 0) w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
+      if (w.lane == 0) w.dstack[WIDX(w, w.nd, (uint32_t)S.vmax, 19)] = *(volatile uint32_t*)&w.ws->tail;
       w.nd++;
       if (w.lane == 0) imply_cd(w, cd, l, no_reason, 0u);
       __syncwarp();
@@ -1015,6 +1154,10 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
   uint32_t iter = 0, conflicts = 0, since_restart = 0, restart_no = 1;
   uint32_t next_reduce = 2000u, reductions = 0;  // periodic database reduction
   uint32_t restart_at = (uint32_t)S.restart_unit * luby_cd(1);
+  // clause sharing with the other jobs of this instance: on for a cube and
+  // once this job has given one away or sees others running
+  bool shared = S.share_lbd > 0 && job != nullptr;
+  unsigned long long share_rd = 0;
   for (;;) {
     if ((++iter & 63u) == 0u) {
       int stop = 0;
@@ -1047,6 +1190,8 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
         abort_code = SCUBA_ERR_INTERNAL;
         return SCUBA_UNKNOWN;
       }
+      if (shared && n <= SHARE_MAXLEN && (n == 1 || lbd <= S.share_lbd))
+        share_publish(S, w, cd, n, lbd, slot);
       w.inc *= (1.0f / 0.95f);
       if (w.lane == 0) w.ws->conflict = 0;
       const uint32_t target = max(blev, w.nd_fixed);
@@ -1093,6 +1238,12 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
       } else {
         backjump_cd(w, cd, w.nd_fixed);
       }
+      if (S.share_lbd > 0 && !shared) {
+        uint32_t others = 0;
+        if (w.lane == 0) others = *(volatile uint32_t*)&S.pending[unit] > 1u;
+        shared = __shfl_sync(FULL, others, 0) != 0u;
+      }
+      if (shared && !share_import(S, w, cd, slot, share_rd)) return SCUBA_UNSAT;
       continue;
     }
     WCOUNT(w, act_reads, w.V - *(volatile uint32_t*)&w.ws->tail);
@@ -1133,6 +1284,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
               export_clauses(w, cd, S.job_cls + (size_t)cell * JOB_CLS_WORDS);
             })) {
           w.nd_fixed = k + 1;
+          shared = S.share_lbd > 0;
           if (w.lane == 0) {
             atomicAdd(&S.ctrl->jobs_split, 1u);
             if (S.prof) {
@@ -1151,7 +1303,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
     w.decisions++;
     WCOUNT(w, decisions, 1);
     const uint32_t lit = 2u * v + ((cd.mark[v] & MK_PHASE) ? 0u : 1u);
-    if (w.lane == 0) w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
+    if (w.lane == 0) w.dstack[WIDX(w, w.nd, (uint32_t)S.vmax, 19)] = *(volatile uint32_t*)&w.ws->tail;
     w.nd++;
     if (w.lane == 0) imply_cd(w, cd, lit, no_reason, 0u);
     __syncwarp();

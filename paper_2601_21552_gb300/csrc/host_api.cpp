@@ -55,7 +55,7 @@ extern "C" {
 
 const char* scuba_last_error(void) { return scuba::g_err.c_str(); }
 
-int scuba_version(void) { return 1; }
+int scuba_version(void) { return 2; }
 
 int scuba_encode_batch(int32_t n, const int64_t* irs, const int64_t* ir_offsets,
                        int32_t nthreads, scuba_encoded** out) {
@@ -63,6 +63,7 @@ int scuba_encode_batch(int32_t n, const int64_t* irs, const int64_t* ir_offsets,
     scuba::set_error("scuba_encode_batch: bad arguments");
     return SCUBA_ERR_ARG;
   }
+  scuba::NvtxRange range("scuba encode");
   scuba_encoded* enc = nullptr;
   try {
     enc = new scuba_encoded;
@@ -184,6 +185,7 @@ int scuba_verify_batch(const scuba_encoded* enc, const int64_t* irs, const int64
                        const uint8_t* verdict, const uint8_t* model, int32_t nthreads,
                        uint8_t* ok) {
   if (!enc || !irs || !ir_offsets || !verdict || !model || !ok) return SCUBA_ERR_ARG;
+  scuba::NvtxRange range("scuba verify");
   const int n = (int)enc->cnf.size();
   std::vector<int64_t> vb(n + 1, 0);
   for (int i = 0; i < n; i++) vb[i + 1] = vb[i] + enc->cnf[i].nvars;

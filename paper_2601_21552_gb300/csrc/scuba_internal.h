@@ -1,10 +1,22 @@
 // scuba_internal.h -- declarations shared by the translation units of libscuba.
 #pragma once
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
 
 namespace scuba {
+
+// A named NVTX range over a scope (encode, upload, prep, search, verify), so a
+// profiler's timeline shows where a call spends its time. NVTX is header-only
+// and costs next to nothing when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // A CNF in DIMACS numbering (+-v, v in 1..nvars) as produced by the encoder.
 struct HostCnf {

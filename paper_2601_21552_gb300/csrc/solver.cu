@@ -50,6 +50,9 @@ constexpr int MAX_PREFIX = 248;   // literals in a split job's prefix
 // Learned clauses a clause-learning donor attaches to a cube: [count, words
 // used, offset of each clause (JOB_CLS_MAX), records {len, lbd, literals}].
 constexpr uint32_t JOB_CLS_MAX = 256, JOB_CLS_WORDS = 4096;
+// Clause-learning records shared between the jobs of one instance: {seq,
+// instance, len | lbd << 8, producer slot, up to SHARE_MAXLEN literals}.
+constexpr uint32_t SHARE_REC = 16, SHARE_MAXLEN = 12;
 
 __device__ __forceinline__ uint32_t code_of(int32_t l) {
   int32_t v = l > 0 ? l : -l;
@@ -74,10 +77,35 @@ struct Ctrl {
   uint32_t q_head, q_tail;
   uint64_t t0;          // globaltimer at launch
   uint32_t jobs_split;  // statistics
-  uint32_t pad;
+  int32_t check_site;   // checked build: site of the first failed bounds check (0: none)
+  uint64_t check_index; // ... the index it saw
+  uint64_t check_limit; // ... and the bound it broke
 };
 
 __device__ void fail_batch(Ctrl* c, int32_t st) { atomicCAS(&c->status, 0, st); }
+
+// Bounds checks of the checked build (-DSCUBA_CHECKED; compute-sanitizer is
+// not available everywhere). SCUBA_IDX(ctrl, i, limit, site) is i when
+// i < limit; otherwise the first failure records its site, index and bound,
+// the call's status becomes SCUBA_ERR_INTERNAL and the access goes to index 0
+// instead, so it stays inside its buffer (the call's results are void from
+// then on). Without SCUBA_CHECKED the macro is the index itself.
+#ifdef SCUBA_CHECKED
+__device__ __noinline__ uint64_t check_fail(Ctrl* c, uint64_t i, uint64_t lim, int site) {
+  if (atomicCAS(&c->check_site, 0, site) == 0) {
+    c->check_index = i;
+    c->check_limit = lim;
+  }
+  fail_batch(c, -8 /* SCUBA_ERR_INTERNAL */);
+  return 0;
+}
+#define SCUBA_IDX(ctrl, i, lim, site)                                                  \
+  (((uint64_t)(i) < (uint64_t)(lim)) ? (i)                                            \
+                                     : (decltype(+(i)))::scuba::dev::check_fail(      \
+                                           (ctrl), (uint64_t)(i), (uint64_t)(lim), (site)))
+#else
+#define SCUBA_IDX(ctrl, i, lim, site) (i)
+#endif
 
 __device__ __forceinline__ bool batch_failed(Ctrl* c) {
   return *(volatile int32_t*)&c->status != 0;
@@ -430,6 +458,13 @@ struct Solve {
   uint32_t* job_cls;           // [ring_cap][JOB_CLS_WORDS] clauses shared with a cube
   uint32_t* cls_copy;          // [slots][JOB_CLS_WORDS] a taken cube's clauses
   int restart_unit;            // conflicts per Luby unit
+  // clauses shared between the jobs (cubes, units) of one instance: pool
+  // (inst & share_mask) is a ring of share_cap records of SHARE_REC words
+  uint32_t* share;             // [pools][share_cap][SHARE_REC]
+  unsigned long long* share_cur;  // [pools] records reserved so far
+  uint32_t share_mask;         // pools - 1 (a power of two)
+  uint32_t share_cap;          // records per pool (a power of two)
+  uint32_t share_lbd;          // publish learned clauses of LBD <= this; 0: off
 };
 
 struct WarpShared {
@@ -477,7 +512,25 @@ struct Warp {
   uint32_t* lvlcnt;        // trace: per-level conflict counts of this slot
   int64_t* lvl_node;       // trace: node of each open level
   __nv_bfloat16* xtile;    // learned: 32 x NFEAT feature tile in shared memory
+#ifdef SCUBA_CHECKED
+  Ctrl* ck;                // where a failed bounds check is recorded
+  uint32_t ent_end;        // occurrence entries of the instance (occ[2V])
+#endif
 };
+
+// A checked index into a buffer of the current warp's instance.
+#define WIDX(w, i, lim, site) SCUBA_IDX((w).ck, (i), (lim), (site))
+
+// Checked build: the instance's bounds for WIDX (a no-op otherwise).
+__device__ __forceinline__ void warp_checks(Warp& w, Ctrl* c) {
+#ifdef SCUBA_CHECKED
+  w.ck = c;
+  w.ent_end = __ldg(&w.occ[2u * w.V]);
+#else
+  (void)w;
+  (void)c;
+#endif
+}
 
 #define WCOUNT(w, field, amount)                 \
   do {                                           \
@@ -494,14 +547,14 @@ __device__ __forceinline__ void record_conflict(Warp& w, uint32_t a, uint32_t b,
 
 // Assign literal l true. Returns false on a clash with the opposite value.
 __device__ __forceinline__ bool imply(Warp& w, uint32_t l) {
-  uint32_t v = l >> 1;
+  uint32_t v = WIDX(w, l >> 1, w.V, 1);
   uint32_t sh = (v & 15u) * 2u;
   uint32_t mask = ((l & 1u) ? 2u : 1u) << sh;
   uint32_t old = atomicOr(&w.asg[v >> 4], mask);
   uint32_t ob = (old >> sh) & 3u;
   if (ob == 0u) {
     uint32_t pos = atomicAdd(&w.ws->tail, 1u);
-    w.trail[pos] = l;
+    w.trail[WIDX(w, pos, w.V, 2)] = l;
     return true;
   }
   if (ob == (mask >> sh)) return true;
@@ -533,11 +586,13 @@ __device__ void eval_long(Warp& w, uint32_t local, uint32_t f) {
 
 // Visit one occurrence entry of the falsified literal f.
 __device__ __forceinline__ void eval_entry(Warp& w, uint32_t f, uint64_t e) {
-  const uint32_t a = (uint32_t)e, b = (uint32_t)(e >> 32);
-  if (a & LONG_CLAUSE) {
-    eval_long(w, a & ~LONG_CLAUSE, f);
+  const uint32_t a0 = (uint32_t)e, b0 = (uint32_t)(e >> 32);
+  if (a0 & LONG_CLAUSE) {
+    eval_long(w, a0 & ~LONG_CLAUSE, f);
     return;
   }
+  const uint32_t a = WIDX(w, a0, 2u * w.V, 3);
+  const uint32_t b = b0 == NONE ? NONE : WIDX(w, b0, 2u * w.V, 3);
   const uint32_t va = lit_value(w.asg, a);
   if (b == NONE) {  // binary (f | a)
     if (va == LV_T || va == LV_X) return;
@@ -577,15 +632,16 @@ __device__ __forceinline__ bool bcp_rounds(Warp& w, Visit&& visit, Round&& on_ro
       const uint32_t nlit = min(32u, hi - base);
       if (nlit == 1) {
         // one literal: every lane reads the same list bounds (broadcast)
-        const uint32_t f = w.trail[base] ^ 1u;
+        const uint32_t f = WIDX(w, w.trail[base] ^ 1u, 2u * w.V, 4);
         const uint32_t beg = __ldg(&w.occ[f]);
         const uint32_t cnt = __ldg(&w.occ[f + 1]) - beg;
         WCOUNT(w, visits, cnt);
-        for (uint32_t e = w.lane; e < cnt; e += 32) visit(f, __ldg(&w.ent[beg + e]));
+        for (uint32_t e = w.lane; e < cnt; e += 32)
+          visit(f, __ldg(&w.ent[WIDX(w, beg + e, w.ent_end, 5)]));
       } else {
         uint32_t f = 0, beg = 0, cnt = 0;
         if (w.lane < nlit) {
-          f = w.trail[base + w.lane] ^ 1u;  // the literal that became false
+          f = WIDX(w, w.trail[base + w.lane] ^ 1u, 2u * w.V, 4);  // the literal that became false
           beg = __ldg(&w.occ[f]);
           cnt = __ldg(&w.occ[f + 1]) - beg;
         }
@@ -613,7 +669,7 @@ __device__ __forceinline__ bool bcp_rounds(Warp& w, Visit&& visit, Round&& on_ro
           const uint32_t jbeg = __shfl_sync(FULL, beg, j);
           const uint32_t jex = __shfl_sync(FULL, excl, j);
           const uint32_t jf = __shfl_sync(FULL, f, j);
-          if (e < total) visit(jf, __ldg(&w.ent[jbeg + (e - jex)]));
+          if (e < total) visit(jf, __ldg(&w.ent[WIDX(w, jbeg + (e - jex), w.ent_end, 5)]));
         } else {
           for (uint32_t e0 = 0; e0 < total; e0 += 32) {
             const uint32_t e = e0 + w.lane;
@@ -630,7 +686,7 @@ __device__ __forceinline__ bool bcp_rounds(Warp& w, Visit&& visit, Round&& on_ro
             const uint32_t jbeg = __shfl_sync(FULL, beg, j);
             const uint32_t jex = __shfl_sync(FULL, excl, j);
             const uint32_t jf = __shfl_sync(FULL, f, j);
-            if (e < total) visit(jf, __ldg(&w.ent[jbeg + (e - jex)]));
+            if (e < total) visit(jf, __ldg(&w.ent[WIDX(w, jbeg + (e - jex), w.ent_end, 5)]));
           }
         }
       }
@@ -1115,6 +1171,7 @@ __device__ int run_job_body(const Solve& S, Warp& w, int unit, int inst, const T
   w.occ = S.occ_begin + S.occ_base[inst];
   const int64_t lbase = S.icb[inst] < S.icb[inst + 1] ? S.cb[S.icb[inst]] : 0;
   w.ent = S.ent + lbase;
+  warp_checks(w, S.ctrl);
   w.head = 0;
   w.nd = 0;
   w.nd_fixed = 0;
@@ -1147,7 +1204,7 @@ __device__ int run_job_body(const Solve& S, Warp& w, int unit, int inst, const T
       if (val == LV_F) return SCUBA_UNSAT;
       if (val == LV_T) continue;
       if (w.lane == 0) {
-        w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail | FLIP;
+        w.dstack[WIDX(w, w.nd, (uint32_t)w.S->vmax, 6)] = *(volatile uint32_t*)&w.ws->tail | FLIP;
         imply(w, l);
       }
       w.nd++;
@@ -1235,7 +1292,7 @@ __device__ int run_job_body(const Solve& S, Warp& w, int unit, int inst, const T
     w.decisions++;
     WCOUNT(w, decisions, 1);
     if (w.lane == 0) {
-      w.dstack[w.nd] = *(volatile uint32_t*)&w.ws->tail;
+      w.dstack[WIDX(w, w.nd, (uint32_t)w.S->vmax, 6)] = *(volatile uint32_t*)&w.ws->tail;
       imply(w, 2u * v + 1u);  // false first
     }
     w.nd++;
@@ -1464,6 +1521,7 @@ __global__ void __launch_bounds__(256) k_propagate(const __grid_constant__ PropA
     w.occ = A.occ_begin + A.occ_base[i];
     const int64_t lbase = A.icb[i] < A.icb[i + 1] ? A.cb[A.icb[i]] : 0;
     w.ent = A.ent + lbase;
+    warp_checks(w, A.ctrl);
     w.head = 0;
     const uint32_t nwords = (w.V + 15u) >> 4;
     for (uint32_t k = lane; k < nwords; k += 32) w.asg[k] = 0u;
@@ -1526,6 +1584,9 @@ __global__ void k_init_ctrl(Ctrl* c, uint32_t n) {
   c->q_tail = 0;
   c->t0 = globaltimer();
   c->jobs_split = 0;
+  c->check_site = 0;
+  c->check_index = 0;
+  c->check_limit = 0;
 }
 
 }  // namespace dev
@@ -1546,6 +1607,7 @@ struct Scratch {
   Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
   Buf lvlcnt, lvl_node;
   Buf cd_reason, cd_pos, cd_level, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
+  Buf share, share_cur;
   Buf job_cls, cls_copy;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
   int sms = 0;
@@ -1620,6 +1682,10 @@ struct UnitArgs {
   const int32_t* asm_lits;
   const int64_t* model_begin;
 };
+
+// clause-sharing pools of the clause-learning search: instance i uses pool
+// i & (kSharePools - 1), a ring of kShareCap records of 64 bytes (128 MiB)
+constexpr uint32_t kSharePools = 1024, kShareCap = 2048;
 
 static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model,
                       cudaStream_t st, const scuba_options* opt, const UnitArgs* ua = nullptr) {
@@ -1771,7 +1837,9 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
         ensure(S.cd_arena, 4 * (size_t)slots * arena_words) ||
         ensure(S.cd_clidx, 4 * (size_t)slots * (arena_words / 8)) ||
         ensure(S.job_cls, 4 * (size_t)ring_cap * dev::JOB_CLS_WORDS) ||
-        ensure(S.cls_copy, 4 * (size_t)slots * dev::JOB_CLS_WORDS)) {
+        ensure(S.cls_copy, 4 * (size_t)slots * dev::JOB_CLS_WORDS) ||
+        ensure(S.share, 4 * (size_t)kSharePools * kShareCap * dev::SHARE_REC) ||
+        ensure(S.share_cur, 8 * (size_t)kSharePools)) {
       set_error("scuba_solve_batch: out of device memory for clause-learning scratch");
       return SCUBA_ERR_NOMEM;
     }
@@ -1798,6 +1866,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   pr.vb = b->inst_var_begin;
   pr.ctrl = P<dev::Ctrl>(S.ctrl);
 
+  NvtxRange prep_range("scuba prep + search launch");
   dev::k_init_ctrl<<<1, 1, 0, st>>>(pr.ctrl, (uint32_t)n_units);
   cudaMemsetAsync(pr.occ_cnt, 0, 4 * (size_t)occ_total, st);
   cudaMemsetAsync(pr.flags, 0, 4 * (size_t)n, st);
@@ -1876,6 +1945,22 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.cls_copy = P<uint32_t>(S.cls_copy);
   sv.cd_arena_words = arena_words;
   sv.restart_unit = opt->restart_unit > 0 ? opt->restart_unit : 100;
+  sv.share = nullptr;
+  sv.share_cur = nullptr;
+  sv.share_mask = 0;
+  sv.share_cap = 0;
+  sv.share_lbd = 0;
+  if (mode == dev::MODE_CDCL && opt->share_lbd >= 0) {
+    // the pools start empty every call: a record left by an earlier batch must
+    // never pass for one of this batch
+    sv.share = P<uint32_t>(S.share);
+    sv.share_cur = P<unsigned long long>(S.share_cur);
+    sv.share_mask = kSharePools - 1;
+    sv.share_cap = kShareCap;
+    sv.share_lbd = opt->share_lbd > 0 ? (uint32_t)opt->share_lbd : 4u;
+    cudaMemsetAsync(sv.share, 0, 4 * (size_t)kSharePools * kShareCap * dev::SHARE_REC, st);
+    cudaMemsetAsync(sv.share_cur, 0, 8 * (size_t)kSharePools, st);
+  }
   std::memset(&sv.tr, 0, sizeof(sv.tr));
   if (mode == dev::MODE_TRACE) {
     const scuba_trace* T = opt->trace;
@@ -1956,7 +2041,13 @@ extern "C" int scuba_sync_status(void* stream) {
   dev::Ctrl c;
   e = cudaMemcpy(&c, it->second.ctrl.p, sizeof(c), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail("cudaMemcpy", e);
-  if (c.status != 0) set_error("device status " + std::to_string(c.status));
+  if (c.status != 0) {
+    std::string msg = "device status " + std::to_string(c.status);
+    if (c.check_site != 0)
+      msg += " (bounds check " + std::to_string(c.check_site) + " failed: index " +
+             std::to_string(c.check_index) + ", limit " + std::to_string(c.check_limit) + ")";
+    set_error(msg);
+  }
   return c.status;
 }
 
@@ -1978,6 +2069,7 @@ extern "C" int scuba_solve_batch_host(const scuba_cnf_batch* hb, uint8_t* verdic
       ensure(S.h_stats, 8 * SCUBA_NSTATS * (size_t)n))
     return SCUBA_ERR_NOMEM;
   cudaError_t e;
+  NvtxRange range("scuba host-buffer solve (upload, solve, download)");
   e = cudaMemcpyAsync(S.h_icb.p, hb->inst_clause_begin, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(S.h_cb.p, hb->clause_begin, 8 * (size_t)(C + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && L > 0) e = cudaMemcpyAsync(S.h_lits.p, hb->lits, 4 * (size_t)L, cudaMemcpyHostToDevice, st);
@@ -2018,7 +2110,8 @@ extern "C" void scuba_release(void) {
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
                 &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node,
                 &S.cd_reason, &S.cd_pos, &S.cd_level, &S.cd_mark, &S.cd_wl, &S.cd_pool,
-                &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.job_cls, &S.cls_copy, &S.h_icb,
+                &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.job_cls, &S.cls_copy,
+                &S.share, &S.share_cur, &S.h_icb,
                 &S.h_cb, &S.h_lits,
                 &S.h_nv, &S.h_vb,
                 &S.h_verdict, &S.h_model, &S.h_stats};

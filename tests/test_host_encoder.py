@@ -32,6 +32,17 @@ def test_exports_every_header_symbol(B):
     for name in sorted(names):
         assert hasattr(B._lib, name), name
     assert set(B.EXPORTED) == names
+    # the checked build (device bounds checks) exports the same ABI
+    import ctypes
+    from paper_2601_21552_gb300 import build
+    chk = ctypes.CDLL(build.LIB_CHECKED)
+    for name in sorted(names):
+        assert hasattr(chk, name), name
+    sizes = np.zeros(2, np.int64)
+    chk.scuba_abi_sizes(sizes.ctypes.data_as(ctypes.c_void_p))
+    ref = np.zeros(2, np.int64)
+    B._lib.scuba_abi_sizes(ref.ctypes.data_as(ctypes.c_void_p))
+    assert (sizes == ref).all()
 
 
 def _unit_propagate(nv, clauses, assign):
