@@ -365,7 +365,8 @@ def cpu_baseline(irs, target_s: float = 15.0, seed: int = 7, algo: str = "cdcl",
     # only (the DPLL solver's heavy tail would make one query's time unbounded)
     single = {}
     if algo == "cdcl":
-        k1 = max(8, int(size / threads / 5))
+        # about a fifth of the time budget on one core, at the measured rate
+        k1 = max(8, min(size, int(size / t_used / threads * target_s / 5)))
         t0 = time.perf_counter()
         _, p1 = _oracle_solve(sample[:k1], 1, algo, budget)
         t1 = time.perf_counter() - t0
@@ -439,7 +440,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "verdicts/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tot / len(times), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "strong" if args.config in (3, 5) else "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
             "config": {"workload": name, "config_id": args.config,
                        "instances_per_step": len(items),
                        "propagations_per_s": sum(props) / tot},
@@ -623,6 +625,8 @@ def run_ours(args):
                         learned_depth=args.learned_depth)
         elif arm == "cdcl":
             opts.update(tuned_cdcl, search="cdcl")
+            if args.learnt_words:
+                opts["learnt_words"] = args.learnt_words
         if work.budgets.get(arm):
             opts["decision_budget"] = work.budgets[arm]
         return opts
@@ -743,7 +747,8 @@ def run_ours(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_step"],
         "higher_is_better": True,
-        "scaling": "weak",
+        # configs 3 and 5 are one fixed list however many GPUs split it
+        "scaling": "strong" if args.config in (3, 5) else "weak",
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
@@ -829,6 +834,9 @@ def main():
     ap.add_argument("--queries", type=int, default=4096,
                     help="queries per GPU (profiling runs use smaller cases)")
     ap.add_argument("--width", type=int, default=16, help="input word width in bits")
+    ap.add_argument("--learnt-words", type=int, default=0,
+                    help="clause-learning arena per worker warp in words (0: the library "
+                         "default 2^18; profiling captures use 2^16 to stay within a few GB)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

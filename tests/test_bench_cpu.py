@@ -62,3 +62,20 @@ def test_cpu_baseline_times_the_sample_in_one_pool_call(monkeypatch):
     assert all(t == threads for _, t in calls)
     size = int(c["sample"].split()[0])
     assert calls[1][0] == size and size >= calls[0][0]
+
+
+def test_reference_arm_other_configs():
+    """The reference arm follows --config: config 1's whole list per step,
+    config 5 a bounded sample per step under the GPU arm's conflict budget."""
+    for cfg, extra in (("1", []), ("5", ["--reference-sample", "4"])):
+        r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", cfg,
+                            "--steps", "1", "--warmup", "0"] + extra, cwd=ROOT,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+        assert d["impl"] == "reference" and d["config"]["config_id"] == int(cfg)
+        assert d["value"] > 0
+        if cfg == "1":
+            assert d["config"]["instances_per_step"] == 256 and d["scaling"] == "weak"
+        else:
+            assert d["config"]["instances_per_step"] == 4 and d["scaling"] == "strong"
