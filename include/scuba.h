@@ -189,7 +189,7 @@ typedef struct scuba_options {
                                 <= share_lbd (units always) to a per-instance pool,
                                 and add the others' clauses at each restart; every
                                 learned clause is implied by the formula, so this
-                                never changes a verdict. 0: default 4; < 0: off */
+                                never changes a verdict. 0: default 2; < 0: off */
 } scuba_options;
 
 /* Number of int64 counters per instance in scuba_options.stats. */

@@ -92,16 +92,21 @@ struct WList {       // one literal's learned watch list in the pool
   uint32_t off, len, cap, pad;
 };
 
+// Per assigned variable, one 16-byte record written by one store: the reason
+// (the occurrence entry {a, b} that implied it, or a clause reference in the
+// low word, ~0 for decisions and assumptions), its trail position and level.
+struct VarInfo {
+  uint32_t reason_lo, reason_hi, pos, level;
+};
+
 struct CdWarp {
-  uint64_t* reason;   // [V] occurrence entry {a, b} or clause reference (low word)
-  uint32_t* level;    // [V]
+  VarInfo* var;       // [V] reason, trail position, decision level
   uint8_t* mark;      // [V] MK_PHASE saved phase, MK_SEEN during analysis
   WList* wl;          // [2V] learned watch list per literal code
   uint64_t* pool;     // [pool_cap] watch entries {clause, blocker}
   uint32_t* arena;    // [arena_words]
   uint32_t* cl_off;   // [arena_words / 8] arena offset of each learned clause, oldest first
   uint32_t* learnt;   // [V] clause under construction
-  uint32_t* pos;      // [V] trail position of each assigned variable
   uint2* ring;        // [RING] shared memory: {literal, trail position} of recent claims
   uint2* cand;        // [CAND] shared memory: analysis queue {trail position, literal}
   uint32_t arena_words, pool_cap;
@@ -145,9 +150,8 @@ __device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64
   const uint32_t pos = WIDX(w, atomicAdd(&w.ws->tail, 1u), w.V, 12);
   w.trail[pos] = l;
   cd.ring[pos & (RING - 1u)] = make_uint2(l, pos);
-  cd.pos[v] = pos;
-  cd.reason[v] = why;
-  cd.level[v] = w.nd;
+  *reinterpret_cast<uint4*>(&cd.var[v]) =
+      make_uint4((uint32_t)why, (uint32_t)(why >> 32), pos, w.nd);
   return true;
 }
 
@@ -500,8 +504,9 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
       uint32_t mk = 0, lv = 0, ps = 0;
       if (q != NONE && (p == NONE || v != (p >> 1))) {
         mk = cd.mark[v];  // three independent loads
-        lv = cd.level[v];
-        ps = cd.pos[v];
+        const uint2 pl = *reinterpret_cast<const uint2*>(&cd.var[v].pos);
+        ps = pl.x;
+        lv = pl.y;
         take = !(mk & MK_SEEN) && lv > 0;
       }
       // one lane per variable (a long clause may repeat a literal)
@@ -575,7 +580,8 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
     if (w.lane == 0) cd.mark[p >> 1] &= (uint8_t)~MK_SEEN;
     __syncwarp();
     if (--path == 0) break;
-    const uint64_t why = cd.reason[p >> 1];
+    const uint2 rw = *reinterpret_cast<const uint2*>(&cd.var[p >> 1].reason_lo);
+    const uint64_t why = (uint64_t)rw.x | ((uint64_t)rw.y << 32);
     r0 = (uint32_t)why;
     r1 = (uint32_t)(why >> 32);
     r2 = NONE;
@@ -588,7 +594,7 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
     uint32_t lv = NONE;
     if (k < n) {
       const uint32_t q = cd.learnt[k];
-      lv = cd.level[q >> 1];
+      lv = cd.var[q >> 1].level;
       if (lv > best_l) {
         best_l = lv;
         best_k = k;
@@ -1029,7 +1035,7 @@ __device__ bool share_import(const Solve& S, Warp& w, CdWarp& cd, int64_t slot,
       }
       const bool have = (uint32_t)w.lane < nj;
       const uint32_t val = have ? lit_value_cd(w.asg, my) : LV_F;
-      const uint32_t lvl = have && val == LV_F ? cd.level[my >> 1] : 0u;
+      const uint32_t lvl = have && val == LV_F ? cd.var[my >> 1].level : 0u;
       const uint32_t nf = __ballot_sync(FULL, have && val != LV_F);
       if (nf == 0u) {  // every literal false: the job's assumptions are refuted
         ok_all = false;
@@ -1083,10 +1089,8 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
   CdWarp cd;
   cd.ring = ring;
   cd.cand = ring + RING;
-  cd.pos = S.cd_pos + slot * S.vmax;
+  cd.var = reinterpret_cast<VarInfo*>(S.cd_var) + slot * S.vmax;
   for (uint32_t k = w.lane; k < RING; k += 32) ring[k] = make_uint2(NONE, NONE);
-  cd.reason = S.cd_reason + slot * S.vmax;
-  cd.level = S.cd_level + slot * S.vmax;
   cd.mark = S.cd_mark + slot * S.vmax;
   cd.wl = S.cd_wl + slot * 2 * S.vmax;
   cd.pool = S.cd_pool + slot * S.cd_pool_cap;
@@ -1165,8 +1169,12 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
         if (S.abort_flag && *S.abort_flag) stop = 1;
         else if (globaltimer() - S.ctrl->t0 > S.time_ns) stop = 2;
         else if (*(volatile uint32_t*)&S.done[unit] & 1u) stop = 3;
+#ifdef SCUBA_CHECKED
+        else if (batch_failed(S.ctrl)) stop = 4;  // a bounds check failed: stop
+#endif
       }
       stop = __shfl_sync(FULL, stop, 0);
+      if (stop == 4) { abort_code = SCUBA_ERR_INTERNAL; return SCUBA_UNKNOWN; }
       if (stop == 1) { abort_code = SCUBA_ERR_ABORTED; return SCUBA_UNKNOWN; }
       if (stop == 2) { abort_code = SCUBA_ERR_TIMEOUT; return SCUBA_UNKNOWN; }
       if (stop == 3) return SCUBA_UNSAT;  // the instance is SAT already; this cube is moot

@@ -54,8 +54,9 @@ __global__ void k_init(float* master, uint64_t seed) {
   master[p] = std * sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
-__global__ void k_pack(const float* master, MlpWeights* W) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// Packed weight of parameter p (BF16 matrices transposed as the solver
+// reads them, FP32 biases).
+__device__ __forceinline__ void pack_one(const float* master, MlpWeights* W, int p) {
   if (p < OFF_B1) {
     const int i = p / NHID, j = p % NHID;
     W->w1t[j * NFEAT + i] = __float2bfloat16(master[p]);
@@ -67,6 +68,11 @@ __global__ void k_pack(const float* master, MlpWeights* W) {
     W->b2 = master[p];
     W->pad[0] = W->pad[1] = W->pad[2] = 0.0f;
   }
+}
+
+__global__ void k_pack(const float* master, MlpWeights* W) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < NPARAM) pack_one(master, W, p);
 }
 
 // Stage rows [r, r+16) of x (clipped to [lo, hi)) into a shared 16x16 tile.
@@ -239,22 +245,31 @@ __global__ void __launch_bounds__(128) k_backward(const int64_t* node_row,
     if (gacc[p] != 0.0f) atomicAdd(&grad[p], gacc[p]);
 }
 
-__global__ void k_accum(float* dst, const float* src) {
-  if (threadIdx.x < 2) dst[threadIdx.x] += src[threadIdx.x];
-}
-
-__global__ void k_adam(float* master, float* m, float* v, const float* grad, const float* scale,
-                       float lr, int step) {
+// One training step after a minibatch's gradient: Adam (Kingma and Ba,
+// Algorithm 1; beta 0.9/0.999, eps 1e-8) on the mean gradient over the
+// minibatch's nodes, then the packed weight of each parameter, the epoch's
+// loss sums, and the other gradient buffer cleared for the next minibatch
+// (the two buffers alternate, so nothing here reads what it clears).
+__global__ void k_adam_pack(float* master, float* m, float* v, const float* grad,
+                            float* grad_next, MlpWeights* W, float lr, int step,
+                            float* epoch_loss) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= NPARAM) return;
+  if (p >= NPARAM + 2) return;
+  grad_next[p] = 0.0f;
+  if (p >= NPARAM) {
+    if (epoch_loss) epoch_loss[p - NPARAM] += grad[p];  // summed loss, nodes used
+    return;
+  }
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float s = scale[1] > 0.0f ? 1.0f / scale[1] : 0.0f;  // mean over nodes
+  const float nodes = grad[NPARAM + 1];
+  const float s = nodes > 0.0f ? 1.0f / nodes : 0.0f;  // mean over nodes
   const float gr = grad[p] * s;
   m[p] = b1 * m[p] + (1.0f - b1) * gr;
   v[p] = b2 * v[p] + (1.0f - b2) * gr * gr;
   const float mh = m[p] / (1.0f - powf(b1, (float)step));
   const float vh = v[p] / (1.0f - powf(b2, (float)step));
   master[p] -= lr * mh / (sqrtf(vh) + eps);
+  pack_one(master, W, p);
 }
 
 }  // namespace mlpk
@@ -264,7 +279,7 @@ namespace {
 struct TrainScratch {
   void* dS = nullptr;
   size_t dS_cap = 0;
-  void* grad = nullptr;  // NPARAM + 2 (loss sum, nodes used)
+  void* grad = nullptr;  // 2 x (NPARAM + 2): gradient, loss sum, nodes used (ping-pong)
 };
 
 std::map<int, TrainScratch>& train_scratch() {
@@ -322,11 +337,12 @@ extern "C" int scuba_mlp_forward(const uint16_t* x, int64_t rows, const void* we
   return e == cudaSuccess ? SCUBA_OK : fail("scuba_mlp_forward", e);
 }
 
-static int grad_impl(const scuba_trace* tr, int64_t k0, int64_t k1, const void* weights,
-                     float* grad, float* dS, cudaStream_t st) {
+// The loss and gradient kernels of nodes [k0, k1) into grad (cleared by
+// the caller): per-node softmax cross-entropy, then the backward pass.
+static void grad_kernels(const scuba_trace* tr, int64_t k0, int64_t k1, const void* weights,
+                         float* grad, float* dS, cudaStream_t st) {
   const int64_t nodes = k1 - k0;
-  cudaMemsetAsync(grad, 0, sizeof(float) * (learn::NPARAM + 2), st);
-  if (nodes <= 0) return SCUBA_OK;
+  if (nodes <= 0) return;
   const int lgrid = (int)std::min<int64_t>((nodes + 7) / 8, 65535);
   mlpk::k_node_loss<<<lgrid, 256, 0, st>>>(
       tr->node_row, tr->node_nrows, tr->node_closed, k0, k1,
@@ -338,6 +354,12 @@ static int grad_impl(const scuba_trace* tr, int64_t k0, int64_t k1, const void* 
         tr->node_row, tr->node_nrows, k0 + b, reinterpret_cast<const __nv_bfloat16*>(tr->x),
         static_cast<const learn::MlpWeights*>(weights), dS, grad);
   }
+}
+
+static int grad_impl(const scuba_trace* tr, int64_t k0, int64_t k1, const void* weights,
+                     float* grad, float* dS, cudaStream_t st) {
+  cudaMemsetAsync(grad, 0, sizeof(float) * (learn::NPARAM + 2), st);
+  grad_kernels(tr, k0, k1, weights, grad, dS, st);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SCUBA_OK : fail("scuba_mlp_grad", e);
 }
@@ -367,26 +389,28 @@ extern "C" int scuba_mlp_train(const scuba_trace* tr, int64_t nodes, float* mast
     if (cudaMalloc(&S.dS, need) != cudaSuccess) return SCUBA_ERR_NOMEM;
     S.dS_cap = need;
   }
-  if (!S.grad && cudaMalloc(&S.grad, sizeof(float) * (learn::NPARAM + 2)) != cudaSuccess)
+  const size_t gwords = learn::NPARAM + 2;
+  if (!S.grad && cudaMalloc(&S.grad, sizeof(float) * 2 * gwords) != cudaSuccess)
     return SCUBA_ERR_NOMEM;
-  float* grad = static_cast<float*>(S.grad);
+  float* gbuf = static_cast<float*>(S.grad);
   float* dS = static_cast<float*>(S.dS);
   cudaMemsetAsync(adam_m, 0, sizeof(float) * learn::NPARAM, st);
   cudaMemsetAsync(adam_v, 0, sizeof(float) * learn::NPARAM, st);
+  cudaMemsetAsync(gbuf, 0, sizeof(float) * 2 * gwords, st);
   if (epoch_loss) cudaMemsetAsync(epoch_loss, 0, sizeof(float) * 2 * (size_t)epochs, st);
+  // three launches per minibatch: loss, backward, Adam + packing (which also
+  // clears the other gradient buffer for the next minibatch)
   int step = 0;
   for (int ep = 0; ep < epochs; ep++) {
     for (int64_t k0 = 0; k0 < nodes; k0 += batch_nodes) {
       const int64_t k1 = std::min<int64_t>(nodes, k0 + batch_nodes);
-      int r = grad_impl(tr, k0, k1, weights, grad, dS, st);
-      if (r != SCUBA_OK) return r;
+      float* grad = gbuf + (size_t)(step & 1) * gwords;
+      float* grad_next = gbuf + (size_t)((step + 1) & 1) * gwords;
+      grad_kernels(tr, k0, k1, weights, grad, dS, st);
       step++;
-      mlpk::k_adam<<<(learn::NPARAM + 255) / 256, 256, 0, st>>>(
-          master, adam_m, adam_v, grad, grad + learn::NPARAM, lr, step);
-      mlpk::k_pack<<<(learn::NPARAM + 255) / 256, 256, 0, st>>>(
-          master, static_cast<learn::MlpWeights*>(weights));
-      // epoch_loss[2*ep] += summed cross-entropy, [2*ep+1] += nodes used
-      if (epoch_loss) mlpk::k_accum<<<1, 32, 0, st>>>(epoch_loss + 2 * ep, grad + learn::NPARAM);
+      mlpk::k_adam_pack<<<(learn::NPARAM + 2 + 255) / 256, 256, 0, st>>>(
+          master, adam_m, adam_v, grad, grad_next, static_cast<learn::MlpWeights*>(weights),
+          lr, step, epoch_loss ? epoch_loss + 2 * ep : nullptr);
     }
   }
   cudaError_t e = cudaGetLastError();

@@ -99,10 +99,13 @@ __device__ __noinline__ uint64_t check_fail(Ctrl* c, uint64_t i, uint64_t lim, i
   fail_batch(c, -8 /* SCUBA_ERR_INTERNAL */);
   return 0;
 }
-#define SCUBA_IDX(ctrl, i, lim, site)                                                  \
-  (((uint64_t)(i) < (uint64_t)(lim)) ? (i)                                            \
-                                     : (decltype(+(i)))::scuba::dev::check_fail(      \
-                                           (ctrl), (uint64_t)(i), (uint64_t)(lim), (site)))
+// The index expression is evaluated exactly once (it may be an atomicAdd).
+template <class T>
+__device__ __forceinline__ T checked_idx(Ctrl* c, T i, uint64_t lim, int site) {
+  return (uint64_t)i < lim ? i : (T)check_fail(c, (uint64_t)i, lim, site);
+}
+#define SCUBA_IDX(ctrl, i, lim, site) \
+  ::scuba::dev::checked_idx((ctrl), (i), (uint64_t)(lim), (site))
 #else
 #define SCUBA_IDX(ctrl, i, lim, site) (i)
 #endif
@@ -445,9 +448,7 @@ struct Solve {
   uint32_t* lvlcnt;            // [slots][MAX_TRACE_DEPTH][vmax] conflict counts
   int64_t* lvl_node;           // [slots][MAX_TRACE_DEPTH] node of each open level
   // conflict-driven clause learning (per slot)
-  uint64_t* cd_reason;         // [slots][vmax]
-  uint32_t* cd_pos;            // [slots][vmax]
-  uint32_t* cd_level;          // [slots][vmax]
+  uint4* cd_var;               // [slots][vmax] reason, trail position, level (16 B)
   uint8_t* cd_mark;            // [slots][vmax]
   WList* cd_wl;                // [slots][2 vmax] learned watch lists
   uint64_t* cd_pool;           // [slots][cd_pool_cap] watch entries
@@ -1220,8 +1221,12 @@ __device__ int run_job_body(const Solve& S, Warp& w, int unit, int inst, const T
         if (S.abort_flag && *S.abort_flag) stop = 1;
         else if (globaltimer() - S.ctrl->t0 > S.time_ns) stop = 2;
         else if (*(volatile uint32_t*)&S.done[unit] & 1u) stop = 3;  // solved elsewhere
+#ifdef SCUBA_CHECKED
+        else if (batch_failed(S.ctrl)) stop = 4;  // a bounds check failed: stop
+#endif
       }
       stop = __shfl_sync(FULL, stop, 0);
+      if (stop == 4) { abort_code = SCUBA_ERR_INTERNAL; return SCUBA_UNKNOWN; }
       if (stop == 1) { abort_code = SCUBA_ERR_ABORTED; return SCUBA_UNKNOWN; }
       if (stop == 2) { abort_code = SCUBA_ERR_TIMEOUT; return SCUBA_UNKNOWN; }
       if (stop == 3) return SCUBA_UNSAT;  // the instance is SAT already; this subtree is moot
@@ -1606,7 +1611,7 @@ struct Scratch {
   Buf occ_base, norm, occ_cnt, occ_begin, ent, units, nunits, flags;
   Buf pending, done, inst_dec, trail, dstack, act, ring, job_act, prefix, ctrl;
   Buf lvlcnt, lvl_node;
-  Buf cd_reason, cd_pos, cd_level, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
+  Buf cd_var, cd_mark, cd_wl, cd_pool, cd_learnt, cd_arena, cd_clidx;
   Buf share, share_cur;
   Buf job_cls, cls_copy;
   Buf h_icb, h_cb, h_lits, h_nv, h_vb, h_verdict, h_model, h_stats;  // for the host entry
@@ -1827,9 +1832,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
       set_error("scuba_solve_batch: learnt_words must be at least max(max_vars + 8, 64)");
       return SCUBA_ERR_ARG;
     }
-    if (ensure(S.cd_reason, 8 * (size_t)slots * vmax) ||
-        ensure(S.cd_pos, 4 * (size_t)slots * vmax) ||
-        ensure(S.cd_level, 4 * (size_t)slots * vmax) ||
+    if (ensure(S.cd_var, 16 * (size_t)slots * vmax) ||
         ensure(S.cd_mark, (size_t)slots * vmax) ||
         ensure(S.cd_wl, 32 * (size_t)slots * vmax) ||
         ensure(S.cd_pool, 8 * (size_t)slots * arena_words) ||
@@ -1931,9 +1934,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.trace_depth = 0;
   sv.lvlcnt = nullptr;
   sv.lvl_node = nullptr;
-  sv.cd_reason = P<uint64_t>(S.cd_reason);
-  sv.cd_pos = P<uint32_t>(S.cd_pos);
-  sv.cd_level = P<uint32_t>(S.cd_level);
+  sv.cd_var = P<uint4>(S.cd_var);
   sv.cd_mark = P<uint8_t>(S.cd_mark);
   sv.cd_wl = P<dev::WList>(S.cd_wl);
   sv.cd_pool = P<uint64_t>(S.cd_pool);
@@ -1957,7 +1958,7 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
     sv.share_cur = P<unsigned long long>(S.share_cur);
     sv.share_mask = kSharePools - 1;
     sv.share_cap = kShareCap;
-    sv.share_lbd = opt->share_lbd > 0 ? (uint32_t)opt->share_lbd : 4u;
+    sv.share_lbd = opt->share_lbd > 0 ? (uint32_t)opt->share_lbd : 2u;
     cudaMemsetAsync(sv.share, 0, 4 * (size_t)kSharePools * kShareCap * dev::SHARE_REC, st);
     cudaMemsetAsync(sv.share_cur, 0, 8 * (size_t)kSharePools, st);
   }
@@ -2109,7 +2110,7 @@ extern "C" void scuba_release(void) {
   Buf* all[] = {&S.occ_base, &S.norm, &S.occ_cnt, &S.occ_begin, &S.ent, &S.units, &S.nunits,
                 &S.flags, &S.pending, &S.done, &S.inst_dec, &S.trail, &S.dstack, &S.act,
                 &S.ring, &S.job_act, &S.prefix, &S.ctrl, &S.lvlcnt, &S.lvl_node,
-                &S.cd_reason, &S.cd_pos, &S.cd_level, &S.cd_mark, &S.cd_wl, &S.cd_pool,
+                &S.cd_var, &S.cd_mark, &S.cd_wl, &S.cd_pool,
                 &S.cd_learnt, &S.cd_arena, &S.cd_clidx, &S.job_cls, &S.cls_copy,
                 &S.share, &S.share_cur, &S.h_icb,
                 &S.h_cb, &S.h_lits,

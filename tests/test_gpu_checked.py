@@ -35,7 +35,7 @@ out = {}
 cases = {"config1": queries.config1(256)[0], "config2_w10": queries.config2(256, w=10)[0]}
 for name, irs in cases.items():
     for search in ("dpll", "cdcl"):
-        res = api.solve_queries(irs, search=search, time_budget_ms=120000)
+        res = api.solve_queries(irs, search=search, time_budget_ms=30000)
         ref = oracle.solve_queries(irs, algo=search)["verdict"]
         out[name + "_" + search] = {"status": int(res["status"]), "msg": B.last_error(),
                                     "same": bool((res["verdict"] == ref).all()),
@@ -46,7 +46,7 @@ for s in range(64):
     n, l = queries.random_3sat(7700 + s, 40, 80)
     inst.append((n, [list(map(int, c)) for c in l]))
 for search in ("dpll", "cdcl"):
-    st, v, m, vb, _ = solve_raw(api, inst, search=search)
+    st, v, m, vb, _ = solve_raw(api, inst, search=search, time_budget_ms=30000)
     ok = all(model_ok(inst[i][1], m, vb[i]) for i in range(len(inst)) if v[i] == 1)
     out["3sat_" + search] = {"status": int(st), "msg": B.last_error(), "models_ok": bool(ok),
                              "verdicts": [int(x) for x in v]}
@@ -61,7 +61,7 @@ def test_checked_build_clean_on_well_formed_inputs():
         pytest.skip("no CUDA device")
     env = dict(os.environ, SCUBA_LIBRARY="checked")
     r = subprocess.run([sys.executable, "-c", "ROOT = %r\n" % ROOT + CHILD], env=env,
-                       capture_output=True, text=True, timeout=900)
+                       capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
     line = [l for l in r.stdout.splitlines() if l.startswith("RESULT ")][-1]
     out = json.loads(line[len("RESULT "):])

@@ -67,3 +67,17 @@ def test_solve_units_rejects_bad_offsets_on_the_host(begin, lits):
                                enc=types.SimpleNamespace(inst_num_vars=np.array([3], np.int32)))
     with pytest.raises(ValueError):
         api.solve_units(db, [0, 0, 0], np.array(begin, np.int64), np.array(lits, np.int32))
+
+
+def test_pick_prefers_steady_setting_within_five_percent():
+    from paper_2601_21552_gb300 import autotune
+    trials = [{"options": {"a": 1}, "mean_s": 1.00, "median_s": 0.7, "times": [0.7, 0.7, 1.6]},
+              {"options": {"a": 2}, "mean_s": 1.04, "median_s": 1.05, "times": [1.0, 1.05, 1.07]},
+              {"options": {"a": 3}, "mean_s": 1.20, "median_s": 1.2, "times": [1.2, 1.2, 1.2]}]
+    assert autotune.pick(trials)["options"] == {"a": 2}   # the lowest mean has a tail
+    trials[1]["mean_s"] = 1.06  # outside 5 %: the lowest mean wins again
+    assert autotune.pick(trials)["options"] == {"a": 1}
+    trials[0]["times"] = [0.9, 1.0, 1.1]
+    trials[0]["median_s"] = 1.0
+    trials[1]["mean_s"] = 1.01  # both steady: the lower mean
+    assert autotune.pick(trials)["options"] == {"a": 1}
