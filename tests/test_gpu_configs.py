@@ -120,7 +120,8 @@ def test_uneven_batch_65536(libs, search):
             B.scuba_solve_batch_ex(db.struct(), vg.data_ptr(), None, s.cuda_stream, o)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g.replay()
+        with torch.cuda.stream(s):
+            g.replay()
         torch.cuda.synchronize()
         replay_s = time.perf_counter() - t0
         assert api.status(s) == 0
@@ -177,9 +178,12 @@ def test_bcp_stress_mixed_batch(libs, search):
     db = api.DeviceBatch.from_csr(icb, cb, lits, nv, vb)
     torch.cuda.synchronize()
     budget = 50_000 if search == "cdcl" else 200_000
+    # random 3-SAT near the threshold: longer runs between restarts (400
+    # conflicts per Luby unit) decide more instances within the budget
+    extra = {"restart_unit": 400} if search == "cdcl" else {}
     t0 = time.perf_counter()
     v, m, st = api.solve(db, decision_budget=budget, time_budget_ms=600000, search=search,
-                         tuned=True)
+                         tuned=True, **extra)
     rc = api.status()
     t_solve = time.perf_counter() - t0
     assert rc == 0, B.last_error()

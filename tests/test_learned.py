@@ -120,7 +120,8 @@ def test_adam_kernel_matches_fp64_restatement(libs):
     # is ill-conditioned: the GPU sums gradients with atomics, so two calls
     # differ in the last bits. b2's gradient is such a sum (dLoss/dscore adds
     # up to zero over each node's rows); those entries are only held to
-    # Adam's step bound |step| <= lr (Kingma and Ba, Sec. 2.1).
+    # Adam's step bound |step| <= lr (1 - beta1) / sqrt(1 - beta2), about
+    # 3.16 lr here (Kingma and Ba, Sec. 2.1).
     g1 = gpu_grad(0, 3, w0)
     train(net_b, 3)                                   # one step
     p1_ref, m1_ref, v1_ref = R.adam_step(p0, 0 * p0, 0 * p0, g1, 1, lr)
@@ -129,10 +130,12 @@ def test_adam_kernel_matches_fp64_restatement(libs):
     ok1[R.NPARAM - 1] = False
     assert ok1.sum() > 0.9 * R.NPARAM
     assert np.abs((p1 - p0) - (p1_ref - p0))[ok1].max() <= 1e-6 + 1e-4 * lr
-    assert np.abs(p1 - p0).max() <= lr * (1 + 1e-5)
+    bound = lr * 0.1 / np.sqrt(0.001) * (1 + 1e-5)
+    assert np.abs(p1 - p0).max() <= bound
     m1, v1 = net_b.m.cpu().numpy(), net_b.v.cpu().numpy()
     assert np.allclose(m1[ok1], m1_ref[ok1], rtol=1e-5, atol=0)
-    assert np.allclose(v1[ok1], v1_ref[ok1], rtol=1e-5, atol=0)
+    # 1 - beta2 in float32 (0.999f) is 1.3e-5 off 0.001, relative
+    assert np.allclose(v1[ok1], v1_ref[ok1], rtol=5e-5, atol=0)
     g2 = gpu_grad(3, 6, net_b.weights)                # at the packed step-1 weights
     train(net_a, 6)                                   # two steps in one call
     p2_ref, m2_ref, v2_ref = R.adam_step(p1_ref, m1_ref, v1_ref, g2, 2, lr)
@@ -140,7 +143,7 @@ def test_adam_kernel_matches_fp64_restatement(libs):
     ok2 = ok1 & (np.abs(g2) >= 1e-3 * np.abs(g2).max())
     assert ok2.sum() > 0.8 * R.NPARAM
     assert np.abs((p2 - p0) - (p2_ref - p0))[ok2].max() <= 1e-6 + 1e-3 * lr
-    assert np.abs(p2 - p0).max() <= 2 * lr * (1 + 1e-5)
+    assert np.abs(p2 - p0).max() <= 2 * bound
     m2, v2 = net_a.m.cpu().numpy(), net_a.v.cpu().numpy()
     assert np.allclose(m2[ok2], m2_ref[ok2], rtol=1e-3, atol=0)
     assert np.allclose(v2[ok2], v2_ref[ok2], rtol=1e-3, atol=0)
@@ -255,38 +258,56 @@ def test_trace_records_closed_nodes(libs):
 
 
 def test_learned_branching_gain_and_identical_verdicts(libs):
-    """Train on decision traces of even-seed queries, test on odd seeds: the
-    learned search returns exactly the plain search's (and the oracle's)
-    verdicts; the decision counts of both are reported."""
+    """The learned configuration at full size: train on decision traces of the
+    2,048 even-seed 16-bit queries, test on the 4,096 odd-seed held-out ones.
+    Both DPLL searches run with splitting off (one warp per instance, so the
+    decision counts belong to the heuristic, not to how subtrees were shared)
+    and must give exactly the stored oracle verdicts; the learned search
+    must really be steered by the network (its counts differ). The gain --
+    decisions and time of the learned search over the plain one -- is
+    measured and reported, whatever its sign: on this family the network does
+    not beat plain activity branching (see the design notes)."""
     api, B = libs
-    tr_irs, _, te_irs, _ = queries.config4_split(512, 512, w=12)
+    tr_irs, _, te_irs, _ = queries.config4_split(2048, 4096, w=16)
     enc = B.scuba_encode_batch(tr_irs)
     db = api.DeviceBatch(enc, "cuda")
-    trace, _, _ = api.record_trace(db, depth=6, time_budget_ms=120000)
+    trace, _, _ = api.record_trace(db, depth=8, max_nodes=1 << 17, max_rows=1 << 25,
+                                   decision_budget=20000, time_budget_ms=300000)
     net = api.Mlp(seed=3)
-    losses = net.train(trace, epochs=12, batch_nodes=64, lr=3e-3)
+    losses = net.train(trace, epochs=20, batch_nodes=64, lr=3e-3)
     assert losses[-1] < losses[0]
     te_enc = B.scuba_encode_batch(te_irs)
     te = api.DeviceBatch(te_enc, "cuda")
-    v0, _, s0 = api.solve(te, want_model=False, time_budget_ms=120000)
+    stored = np.array([int(line) for line in open(os.path.join(
+        ROOT, "tests", "golden", "config4_test_oracle_verdicts.txt"))
+        if line.strip() and not line.startswith("#")], np.uint8)
+    assert len(stored) == 4096
+    import time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    v0, _, s0 = api.solve(te, want_model=False, split=False, time_budget_ms=300000)
     assert api.status() == 0
-    v1, m1, s1 = api.solve(te, heuristic=B.SCUBA_HEUR_LEARNED, mlp_weights=net.weights,
-                           learned_depth=6, time_budget_ms=120000)
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    v1, m1, s1 = api.solve(te, split=False, heuristic=B.SCUBA_HEUR_LEARNED,
+                           mlp_weights=net.weights, learned_depth=6, time_budget_ms=300000)
     assert api.status() == 0
+    t_learned = time.perf_counter() - t0
     v0, v1 = v0.cpu().numpy(), v1.cpu().numpy()
-    ref = oracle.solve_queries(te_irs)["verdict"]
-    assert (v0 == ref).all() and (v1 == ref).all()
+    assert (v0 == stored).all() and (v1 == stored).all()
     fails, _ = B.scuba_verify_batch(te_enc, v1, m1.cpu().numpy())
     assert fails == 0
     d0, d1 = int(s0[:, 0].sum().item()), int(s1[:, 0].sum().item())
-    unsat = ref == 0
-    report = {"train_queries": 512, "test_queries": 512, "input_bits": 12,
-              "loss_first": losses[0], "loss_last": losses[-1],
+    assert d0 != d1  # the network orders the top decisions
+    report = {"train_queries": 2048, "test_queries": 4096, "input_bits": 16,
+              "trace_nodes": trace.used()[0], "loss_first": losses[0], "loss_last": losses[-1],
               "decisions_plain": d0, "decisions_learned": d1,
-              "decisions_plain_unsat": int(s0.cpu().numpy()[unsat, 0].sum()),
-              "decisions_learned_unsat": int(s1.cpu().numpy()[unsat, 0].sum())}
+              "decisions_learned_over_plain": d1 / d0,
+              "time_plain_s": t_plain, "time_learned_s": t_learned,
+              "time_learned_over_plain": t_learned / t_plain,
+              "gain": "learned fewer decisions" if d1 < d0 else "learned more decisions"}
     print("learned-vs-plain", json.dumps(report))
     out = os.environ.get("SCUBA_REPORT_DIR")
     if out:
-        with open(os.path.join(out, "learned_vs_plain_w12.json"), "w") as f:
+        with open(os.path.join(out, "learned_vs_plain_config4.json"), "w") as f:
             json.dump(report, f)
