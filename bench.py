@@ -635,6 +635,8 @@ def run_ours(args):
                 opts["learnt_words"] = args.learnt_words
         if work.budgets.get(arm):
             opts["decision_budget"] = work.budgets[arm]
+        if args.config in (3, 5):  # uneven sizes: largest instances first (LPT)
+            opts["order"] = db.lpt_order()
         opts.update(work.overrides.get(arm, {}))
         return opts
 

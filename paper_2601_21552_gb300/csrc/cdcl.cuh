@@ -68,7 +68,7 @@ constexpr uint32_t NB_T = 1u, NB_F = 2u, NB_FRESH = 4u;  // assignment nibble bi
 constexpr uint32_t RING = 128;  // recent-trail entries per warp in shared memory
 constexpr uint32_t CAND = 96;   // current-level literals awaiting resolution, per warp
 // shared memory per warp for the clause-learning search (16-byte multiple)
-constexpr uint32_t CD_SMEM_WARP = RING * 8 + CAND * 8 + RING * 8;
+constexpr uint32_t CD_SMEM_WARP = RING * 8 + CAND * 8;
 constexpr uint8_t MK_PHASE = 1, MK_SEEN = 2;
 
 // Profile counters (only when the caller passed a profile array): lane 0
@@ -109,7 +109,6 @@ struct CdWarp {
   uint32_t* learnt;   // [V] clause under construction
   uint2* ring;        // [RING] shared memory: {literal, trail position} of recent claims
   uint2* cand;        // [CAND] shared memory: analysis queue {trail position, literal}
-  uint2* rwhy;        // [RING] shared memory: the reason of each ring entry (low, high word)
   uint32_t arena_words, pool_cap;
   uint32_t top;       // first free arena word
   uint32_t ncl;       // learned clauses in the arena
@@ -151,7 +150,6 @@ __device__ __forceinline__ bool imply_cd(Warp& w, CdWarp& cd, uint32_t l, uint64
   const uint32_t pos = WIDX(w, atomicAdd(&w.ws->tail, 1u), w.V, 12);
   w.trail[pos] = l;
   cd.ring[pos & (RING - 1u)] = make_uint2(l, pos);
-  cd.rwhy[pos & (RING - 1u)] = make_uint2((uint32_t)why, (uint32_t)(why >> 32));
   *reinterpret_cast<uint4*>(&cd.var[v]) =
       make_uint4((uint32_t)why, (uint32_t)(why >> 32), pos, w.nd);
   return true;
@@ -314,32 +312,26 @@ __device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f, ui
                               uint32_t cnt) {
   __syncwarp();
   if (cd.top == 0) return;  // no learned clauses
-  if (!__any_sync(FULL, cnt > 0u)) return;  // none watches a literal of this batch
   const long long t0 = pf_now(*w.S);
   uint32_t inc = cnt;
-  if (nlit > 1) {  // one frontier literal (the common case) needs no scan
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, inc, d);
-      if (w.lane >= d) inc += y;
-    }
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, inc, d);
+    if (w.lane >= d) inc += y;
   }
   const uint32_t excl = inc - cnt;
-  const uint32_t total = __shfl_sync(FULL, inc, nlit > 1 ? 31 : 0);
+  const uint32_t total = __shfl_sync(FULL, inc, 31);
   WCOUNT(w, visits, total);
   uint32_t dirty = 0;  // lists that lost an entry
   for (uint32_t e0 = 0; e0 < total; e0 += 32) {
     const uint32_t e = e0 + w.lane;
-    int lo_j = 0;  // owner: smallest lane j with inc_j > e (lane 0 when nlit == 1)
-    if (nlit > 1) {
-      int hi_j = 31;
+    int lo_j = 0, hi_j = 31;  // owner: smallest lane j with inc_j > e
 #pragma unroll
-      for (int s2 = 0; s2 < 5; s2++) {
-        const int mid = (lo_j + hi_j) >> 1;
-        const uint32_t v = __shfl_sync(FULL, inc, mid);
-        if (v > e) hi_j = mid; else lo_j = mid + 1;
-        if (lo_j > hi_j) lo_j = hi_j;
-      }
+    for (int s2 = 0; s2 < 5; s2++) {
+      const int mid = (lo_j + hi_j) >> 1;
+      const uint32_t v = __shfl_sync(FULL, inc, mid);
+      if (v > e) hi_j = mid; else lo_j = mid + 1;
+      if (lo_j > hi_j) lo_j = hi_j;
     }
     const uint32_t jbeg = __shfl_sync(FULL, beg, lo_j);
     const uint32_t jex = __shfl_sync(FULL, excl, lo_j);
@@ -405,15 +397,13 @@ __device__ void learned_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f, ui
 __device__ __forceinline__ void static_batch(Warp& w, CdWarp& cd, uint32_t nlit, uint32_t f,
                                              uint32_t beg, uint32_t cnt) {
   uint32_t inc = cnt;
-  if (nlit > 1) {  // one frontier literal (the common case) needs no scan
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, inc, d);
-      if (w.lane >= d) inc += y;
-    }
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, inc, d);
+    if (w.lane >= d) inc += y;
   }
   const uint32_t excl = inc - cnt;
-  const uint32_t total = __shfl_sync(FULL, inc, nlit > 1 ? 31 : 0);
+  const uint32_t total = __shfl_sync(FULL, inc, 31);
   WCOUNT(w, visits, total);
   for (uint32_t e0 = 0; e0 < total; e0 += 32) {
     const uint32_t e = e0 + w.lane;
@@ -590,13 +580,7 @@ __device__ uint32_t analyze_cd(Warp& w, CdWarp& cd, uint32_t& blev, uint32_t& lb
     if (w.lane == 0) cd.mark[p >> 1] &= (uint8_t)~MK_SEEN;
     __syncwarp();
     if (--path == 0) break;
-    // p's reason: from the shared-memory ring while its slot still holds p's
-    // trail position (both paths above leave idx just below it), else from
-    // the variable's record in global memory
-    const uint32_t ppos = (uint32_t)(idx + 1);
-    uint2 rw;
-    if (cd.ring[ppos & (RING - 1u)].y == ppos) rw = cd.rwhy[ppos & (RING - 1u)];
-    else rw = *reinterpret_cast<const uint2*>(&cd.var[p >> 1].reason_lo);
+    const uint2 rw = *reinterpret_cast<const uint2*>(&cd.var[p >> 1].reason_lo);
     const uint64_t why = (uint64_t)rw.x | ((uint64_t)rw.y << 32);
     r0 = (uint32_t)why;
     r1 = (uint32_t)(why >> 32);
@@ -1105,7 +1089,6 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
   CdWarp cd;
   cd.ring = ring;
   cd.cand = ring + RING;
-  cd.rwhy = ring + RING + CAND;
   cd.var = reinterpret_cast<VarInfo*>(S.cd_var) + slot * S.vmax;
   for (uint32_t k = w.lane; k < RING; k += 32) ring[k] = make_uint2(NONE, NONE);
   cd.mark = S.cd_mark + slot * S.vmax;
