@@ -50,12 +50,12 @@ METRIC = "verdicts/sec + BCP propagations/sec on 1 GB300, learned vs plain, bit-
 
 
 # DRAM traffic of the clause-learning search kernel from one single-pass ncu
-# capture of a full launch (profiles/k_solve_cdcl_partition16.md: 6.61 GB read +
-# 5.45 GB written for 1.4327e8 propagations), per propagation, valid only for
-# the kernel sources it was taken on (sha256 prefix of solver.cu + learn.cuh +
-# cdcl.cuh); scaled to each launch by the propagations it processes.
-PROFILED_SOURCES = "c77c54a6c17b6968"
-DRAM_BYTES_PER_PROPAGATION = {"cdcl": (6.61e9 + 5.45e9) / 1.4327e8}
+# capture of a full bench launch (profiles/k_solve_cdcl_partition16.md: 8.71 GB
+# read + 7.04 GB written for 1.2389e8 propagations), per propagation, valid
+# only for the kernel sources it was taken on (sha256 prefix of solver.cu +
+# learn.cuh + cdcl.cuh); scaled to each launch by the propagations it processes.
+PROFILED_SOURCES = "d559d46d82c2e11f"
+DRAM_BYTES_PER_PROPAGATION = {"cdcl": (8.7077e9 + 7.0410e9) / 1.2389e8}
 
 
 def _kernel_sources_sha() -> str:
@@ -67,11 +67,11 @@ def _kernel_sources_sha() -> str:
     return h.hexdigest()[:16]
 
 
-# L2 traffic of the same kernel from one single-pass ncu capture of a full
-# launch (lts__t_bytes.sum: 135.89 GB for 1.5016e8 propagations;
-# profiles/k_solve_cdcl_partition16.md), per propagation, under the same
-# source hash (idle warps polling the job ring included).
-L2_BYTES_PER_PROPAGATION = {"cdcl": 135.89e9 / 1.5016e8}
+# L2 traffic of the same kernel from the same single-pass ncu capture
+# (lts__t_bytes.sum: 125.93 GB for 1.2389e8 propagations), per propagation,
+# under the same source hash (idle warps polling the job ring and the
+# clause-sharing pools included).
+L2_BYTES_PER_PROPAGATION = {"cdcl": 125.93e9 / 1.2389e8}
 
 
 def l2_probe(dev, mib: int = 32, iters: int = 200) -> float:
