@@ -190,9 +190,6 @@ typedef struct scuba_options {
                                 and add the others' clauses at each restart; every
                                 learned clause is implied by the formula, so this
                                 never changes a verdict. 0: default 2; < 0: off */
-  int32_t split_conflicts;   /* CDCL: a job gives away cubes only after this many
-                                conflicts of its own (a job that has shown itself
-                                hard), besides split_min decisions; 0: no gate */
 } scuba_options;
 
 /* Number of int64 counters per instance in scuba_options.stats. */

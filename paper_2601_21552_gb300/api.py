@@ -128,8 +128,7 @@ def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
             profile: torch.Tensor | None = None, num_inputs: torch.Tensor | None = None,
             trace: "Trace | None" = None, search: str | int = "dpll",
             restart_unit: int = 0, learnt_words: int = 0,
-            split_depth: int = 0, share_lbd: int = 0,
-            split_conflicts: int = 0) -> B.scuba_options:
+            split_depth: int = 0, share_lbd: int = 0) -> B.scuba_options:
     o = B.scuba_options_init()
     o.heuristic = heuristic
     o.search = SEARCH[search] if isinstance(search, str) else int(search)
@@ -137,7 +136,6 @@ def options(heuristic: int = B.SCUBA_HEUR_ACTIVITY, decision_budget: int = 0,
     o.learnt_words = learnt_words
     o.split_depth = split_depth
     o.share_lbd = share_lbd
-    o.split_conflicts = split_conflicts
     o.decision_budget = decision_budget
     o.time_budget_ms = time_budget_ms
     o.split = 1 if split else 0

@@ -41,8 +41,8 @@ SPACE = {
 # Luby restart unit (25) come from a wider sweep over {8, 16, 32} x
 # {12, 25, 40}, and smaller split_min (4-16) and caps (10-18) lost to these
 # on the mean; share_lbd is the LBD bound of the clauses the jobs of one
-# instance share (-1: no sharing); a gate on the job's own conflicts
-# (split_conflicts 8-128) was no better than none
+# instance share (-1: no sharing); a gate on the job's own conflicts before
+# it may give cubes away (8-128) was measured no better than none
 SPACE_CDCL = {
     "split_min": [32, 48, 64],
     "split_depth": [248],

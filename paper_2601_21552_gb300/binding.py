@@ -54,7 +54,7 @@ class scuba_options(ctypes.Structure):
                 ("search_event_begin", _vp), ("search_event_end", _vp),
                 ("inst_num_inputs", _vp), ("trace", _vp), ("search", _i32),
                 ("restart_unit", _i32), ("learnt_words", _i64), ("split_depth", _i32),
-                ("share_lbd", _i32), ("split_conflicts", _i32)]
+                ("share_lbd", _i32)]
 
 
 class scuba_trace(ctypes.Structure):

@@ -1280,8 +1280,7 @@ __device__ int run_cdcl(const Solve& S, Warp& w, int64_t slot, int unit, int ins
     if (S.split && w.decisions >= (uint32_t)S.split_min &&
         (w.decisions % (uint32_t)S.split_interval) == 0 && w.nd > w.nd_fixed &&
         w.nd_fixed + 1 <= (uint32_t)MAX_PREFIX &&
-        w.nd_fixed < asm_levels + (uint32_t)S.split_depth &&
-        conflicts >= (uint32_t)S.split_conflicts) {
+        w.nd_fixed < asm_levels + (uint32_t)S.split_depth) {
       uint32_t idle = 0;
       if (w.lane == 0) idle = *(volatile uint32_t*)&S.ctrl->idle;
       idle = __shfl_sync(FULL, idle, 0);

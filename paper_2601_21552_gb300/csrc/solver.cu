@@ -430,7 +430,6 @@ struct Solve {
   uint32_t ring_cap;       // power of two
   int32_t split_min;       // decisions a job makes before it may donate
   int32_t split_depth;     // CDCL: cube levels below the instance a donor may reach
-  int32_t split_conflicts; // CDCL: conflicts a job makes before it may donate
   Ctrl* ctrl;
   int64_t budget;
   uint64_t time_ns;
@@ -1919,7 +1918,6 @@ static int solve_impl(const scuba_cnf_batch* b, uint8_t* verdict, uint8_t* model
   sv.prefix = P<uint32_t>(S.prefix);
   sv.split_min = opt->split_min > 0 ? opt->split_min : 256;
   sv.split_depth = opt->split_depth > 0 ? opt->split_depth : dev::MAX_PREFIX;
-  sv.split_conflicts = opt->split_conflicts > 0 ? opt->split_conflicts : 0;
   sv.ctrl = P<dev::Ctrl>(S.ctrl);
   sv.budget = opt->decision_budget;
   int64_t tb = opt->time_budget_ms > 0 ? opt->time_budget_ms : 600000;
@@ -2310,7 +2308,6 @@ extern "C" int scuba_solve_batch_noalloc(const scuba_cnf_batch* b, uint8_t* verd
   sv.prefix = static_cast<uint32_t*>(at(o_prefix));
   sv.split_min = opt->split_min > 0 ? opt->split_min : 256;
   sv.split_depth = opt->split_depth > 0 ? opt->split_depth : dev::MAX_PREFIX;
-  sv.split_conflicts = opt->split_conflicts > 0 ? opt->split_conflicts : 0;
   sv.ctrl = pr.ctrl;
   sv.budget = opt->decision_budget;
   int64_t tb = opt->time_budget_ms > 0 ? opt->time_budget_ms : 600000;
