@@ -79,3 +79,39 @@ def test_reference_arm_other_configs():
             assert d["config"]["instances_per_step"] == 256 and d["scaling"] == "weak"
         else:
             assert d["config"]["instances_per_step"] == 4 and d["scaling"] == "strong"
+
+
+def test_parity_rules_and_workloads():
+    """The bench's parity check: every instance must match the stored oracle
+    verdicts on the fully decided configurations; on the budgeted ones (3, 5)
+    every instance both sides decide must match and UNKNOWN is allowed; a
+    disagreement always raises. The host workloads carry the stored verdicts
+    that belong to them."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import pytest
+    import bench
+    from paper_2601_21552_gb300 import binding as B
+
+    w1 = bench.build_work(B, 1, 256, 1)
+    assert w1.n == 256 and len(w1.stored[1]) == 256 and set(w1.arms) == {"cdcl", "plain"}
+    ref = w1.stored[1].copy()
+    assert bench._parity(w1, ref.copy())["checked"] == 256
+    unk = ref.copy()
+    unk[3] = 2
+    with pytest.raises(AssertionError):          # config 1 must be fully decided
+        bench._parity(w1, unk)
+    bad = ref.copy()
+    bad[5] ^= 1
+    with pytest.raises(AssertionError):
+        bench._parity(w1, bad)
+
+    class Budgeted:
+        config = 5
+        stored = ("x", np.array([0, 1, 2, 1, 2], np.uint8))
+    r = bench._parity(Budgeted, np.array([0, 2, 1, 1, 2], np.uint8))
+    assert r["checked"] == 2 and r["oracle_unknown"] == 2 and r["gpu_unknown"] == 2
+    with pytest.raises(AssertionError):
+        bench._parity(Budgeted, np.array([1, 2, 2, 1, 2], np.uint8))
+    w2 = bench.build_work(B, 2, 64, 2, width=8)   # two ranks' worth of one list
+    assert w2.n == 128 and w2.stored is None and len(w2.ninp) == 128
