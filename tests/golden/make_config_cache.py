@@ -8,6 +8,7 @@ budget is stored as UNKNOWN (2), never guessed.
 
     python tests/golden/make_config_cache.py config3 [--budget 20000] [--threads N]
     python tests/golden/make_config_cache.py config5 [--budget 20000] [--threads N]
+    python tests/golden/make_config_cache.py config5 --escalate 100000 --max-vars 300
 
 Workloads (the generators' own definitions, seeds SEED_BASE[c] + i):
   config3  65,536 grown queries, widths 8/16/32, clause targets log-uniform
@@ -96,14 +97,82 @@ def read_cache(path):
     return head, np.frombuffer("".join(digits).encode(), dtype=np.uint8) - ord("0")
 
 
+def escalate(which, budget, max_vars, threads, chunk=256):
+    """Re-solve, at a larger conflict budget, the random 3-SAT instances of
+    the config-5 cache that the first pass left UNKNOWN and that have at most
+    `max_vars` variables (chosen by size alone), and rewrite the cache with
+    their new verdicts and a header line recording the pass. Progress goes to
+    `<output>.escalate.partial`, so an interrupted pass resumes."""
+    if which != "config5":
+        raise SystemExit("escalation is defined for config5 only")
+    out = os.path.join(HERE, FILES[which])
+    head, v = read_cache(out)
+    fp, count, _ = instances(which)
+    if head.get("fingerprint") != fp:
+        raise SystemExit("the cache belongs to other instances")
+    sat = queries.config5_sat(10000)
+    todo = [i for i in range(len(sat)) if v[i] == 2 and sat[i][0] <= max_vars]
+    part = out + ".escalate.partial"
+    got = {}
+    key = f"{fp} {budget} {max_vars}"
+    if os.path.exists(part):
+        with open(part) as f:
+            if f.readline().strip() == key:
+                for line in f:
+                    i, x = line.split()
+                    got[int(i)] = int(x)
+    else:
+        with open(part, "w") as f:
+            f.write(key + "\n")
+    rest = [i for i in todo if i not in got]
+    t0 = time.time()
+    with open(part, "a") as f:
+        for k in range(0, len(rest), chunk):
+            sel = rest[k:k + chunk]
+            cnfs = [oracle.CNF(sat[i][0], np.arange(0, 3 * len(sat[i][1]) + 1, 3, dtype=np.int64),
+                               sat[i][1].reshape(-1)) for i in sel]
+            r = oracle.solve_cnfs(cnfs, threads=threads, budget=budget, algo="cdcl")
+            for i, x in zip(sel, r["verdict"]):
+                got[i] = int(x)
+                f.write(f"{i} {int(x)}\n")
+            f.flush()
+            print(f"{which} escalation: {len(got)}/{len(todo)} ({time.time() - t0:.0f}s)",
+                  flush=True)
+    v = v.copy()
+    for i, x in got.items():
+        v[i] = x
+    decided = sum(1 for x in got.values() if x != 2)
+    lines = open(out).read().splitlines()
+    header = [l for l in lines if l.startswith("#") and not l.startswith(("# sat:", "# unsat:",
+                                                                           "# unknown:"))]
+    header += [f"# escalated: the {len(todo)} UNKNOWN random 3-SAT instances with at most "
+               f"{max_vars} variables re-solved at {budget} conflicts, {decided} decided",
+               f"# sat: {int((v == 1).sum())}", f"# unsat: {int((v == 0).sum())}",
+               f"# unknown: {int((v == 2).sum())}"]
+    digits = "".join(str(int(x)) for x in v)
+    with open(out, "w") as f:
+        f.write("\n".join(header) + "\n")
+        for k in range(0, count, 64):
+            f.write(digits[k:k + 64] + "\n")
+    os.remove(part)
+    print(f"{which}: escalated {len(todo)}, decided {decided}; UNKNOWN now {int((v == 2).sum())}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("which", choices=sorted(FILES))
     ap.add_argument("--budget", type=int, default=20000, help="conflicts per instance")
     ap.add_argument("--threads", type=int, default=0, help="0: all host cores")
     ap.add_argument("--chunk", type=int, default=2048)
+    ap.add_argument("--escalate", type=int, default=0,
+                    help="config5: re-solve the cache's UNKNOWN random 3-SAT instances with "
+                         "at most --max-vars variables at this conflict budget")
+    ap.add_argument("--max-vars", type=int, default=300)
     args = ap.parse_args()
     threads = args.threads or oracle.default_threads()
+    if args.escalate:
+        escalate(args.which, args.escalate, args.max_vars, threads)
+        return
     fp, count, solve = instances(args.which)
     out = os.path.join(HERE, FILES[args.which])
     part = out + ".partial"
