@@ -266,3 +266,40 @@ def test_wrap_queries_encode_equisatisfiably(B):
     want = oracle.solve_queries(irs, max_words=16)["verdict"]
     assert got.tolist() == want.tolist()
     assert set(want.tolist()) == {0, 1}
+
+
+def test_grown_queries_product_cnf_agrees_with_oracle_encoding(B):
+    """The product encoder on the config-3 template family (2-D/3-D ids,
+    row-major scalings, cubic size factors, partitions): the oracle's
+    clause-learning solver decides the product's CNF and the oracle's own
+    encoding of the same query, and the two verdicts agree wherever both
+    are decided; every SAT model of the product CNF passes the host
+    re-verification against the integer constraints."""
+    import oracle
+    irs, meta = queries.config3(400)
+    enc = B.scuba_encode_batch(irs)
+    nc = np.diff(enc.inst_clause_begin)
+    sel = np.argsort(nc, kind="stable")[:48]          # the smallest, every width
+    cnfs = []
+    for i in sel:
+        c0, c1 = enc.inst_clause_begin[i], enc.inst_clause_begin[i + 1]
+        l0 = enc.clause_begin[c0]
+        cnfs.append(oracle.CNF(int(enc.inst_num_vars[i]), enc.clause_begin[c0:c1 + 1] - l0,
+                               enc.lits[l0:enc.clause_begin[c1]]))
+    prod = oracle.solve_cnfs(cnfs, budget=20000, algo="cdcl")["verdict"]
+    own = oracle.solve_queries([irs[i] for i in sel], budget=20000, algo="cdcl")["verdict"]
+    both = (prod != 2) & (own != 2)
+    assert both.sum() >= 40
+    assert (prod[both] == own[both]).all()
+    assert {0, 1} <= set(own[both].tolist())
+    # models of the product CNF, decoded through its input map, satisfy the query
+    verdict = np.full(enc.n, 2, np.uint8)
+    model = np.zeros(enc.total_vars, np.uint8)
+    for k, i in enumerate(sel):
+        if prod[k] == 1:
+            r = oracle.cdcl(cnfs[k])
+            verdict[i] = 1
+            vb = enc.inst_var_begin[i]
+            model[vb:vb + enc.inst_num_vars[i]] = r["model"][:enc.inst_num_vars[i]]
+    fails, ok = B.scuba_verify_batch(enc, verdict, model)
+    assert fails == 0 and (ok[sel][prod == 1] == 1).all()
